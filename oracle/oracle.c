@@ -1,0 +1,247 @@
+/*
+ * CPU oracle for partial modular polynomial evaluation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the CUDA library and includes nothing of it.
+ *
+ * What it computes (paper Sect. 2.3, the definition of the bivariate images
+ * below Eq. 1): for a prime p, terms (a_i, d_i, e_i, M_i) and a point beta in
+ * F_p^{n-2},
+ *
+ *     out[t - t0][g] = sum_{i in group g} a_i * prod_{k=3..n} (beta_k^t)^{e_ik}  mod p
+ *
+ * for t = t0 .. t0+T-1, where group g collects the terms sharing (d_i, e_i)
+ * and groups are numbered in descending lexicographic order of (d, e)
+ * (Sect. 2.3: lex order with x1 > x2 > ... makes like monomials adjacent).
+ *
+ * Arithmetic: every product is (unsigned __int128)a*b % p, every sum is a
+ * compare-and-subtract on values below p < 2^63, every power is binary
+ * square-and-multiply.  Nothing is blocked, fused or reordered.
+ *
+ *   oracle_eval_direct : O1, the definition above.  A per-t table of
+ *                        (beta_k^t)^e for e <= max degree is the only memo.
+ *   oracle_eval_cells  : the same definition for a list of (t, g) cells.
+ *   oracle_eval_matrix : O2, Algorithm 1 of the paper restated: m_i = M_i(beta)
+ *                        from power tables (Sect. 2.3), then T rounds of
+ *                        a_i <- a_i * m_i followed by the coefficient
+ *                        reduction over each group.  It is the CPU baseline.
+ *
+ * Pins (tests under tests/): brute force with exact Python integers on tiny
+ * inputs, Fermat's little theorem at Miller-Rabin-verified primes, the ring
+ * homomorphisms eval(A+B) = eval(A)+eval(B) and eval(A*B) = eval(A)*eval(B),
+ * the t0 = 0 and beta = 1 coefficient sums, the paper's gcd example
+ * (Sect. 2.1) and small symmetric Toeplitz determinants (Sect. 2.2.1).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+/* ---------------------------------------------------------------- F_p ---- */
+
+uint64_t oracle_mulmod(uint64_t a, uint64_t b, uint64_t p)
+{
+    return (uint64_t)(((u128)a * (u128)b) % (u128)p);
+}
+
+/* a, b < p < 2^63, so a + b does not wrap. */
+uint64_t oracle_addmod(uint64_t a, uint64_t b, uint64_t p)
+{
+    uint64_t s = a + b;
+    return s >= p ? s - p : s;
+}
+
+uint64_t oracle_powmod(uint64_t b, uint64_t e, uint64_t p)
+{
+    uint64_t r = 1 % p, x = b % p;
+    while (e) {
+        if (e & 1) r = oracle_mulmod(r, x, p);
+        x = oracle_mulmod(x, x, p);
+        e >>= 1;
+    }
+    return r;
+}
+
+/* -------------------------------------------------------------- groups ---- */
+
+static int cmp_desc_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? 1 : (x > y ? -1 : 0);
+}
+
+static uint64_t term_key(const uint32_t *exps, uint32_t n, uint64_t i)
+{
+    return ((uint64_t)exps[i * n + 0] << 32) | (uint64_t)exps[i * n + 1];
+}
+
+/*
+ * Distinct (d, e) keys in descending lexicographic order.
+ *   keys_out  : capacity 2*s, receives (d, e) pairs of the G groups
+ *   term_group: receives the group index of every term
+ * Returns G.  Requires n >= 2.
+ */
+uint64_t oracle_group_keys(uint32_t n, uint64_t s, const uint32_t *exps,
+                           uint32_t *keys_out, uint64_t *term_group)
+{
+    if (s == 0) return 0;
+    uint64_t *k = (uint64_t *)malloc(s * sizeof(uint64_t));
+    for (uint64_t i = 0; i < s; ++i) k[i] = term_key(exps, n, i);
+    qsort(k, s, sizeof(uint64_t), cmp_desc_u64);
+    uint64_t G = 0;
+    for (uint64_t i = 0; i < s; ++i)
+        if (i == 0 || k[i] != k[G - 1]) k[G++] = k[i];
+    for (uint64_t g = 0; g < G; ++g) {
+        keys_out[2 * g] = (uint32_t)(k[g] >> 32);
+        keys_out[2 * g + 1] = (uint32_t)(k[g] & 0xffffffffu);
+    }
+    for (uint64_t i = 0; i < s; ++i) {           /* binary search, descending */
+        uint64_t key = term_key(exps, n, i), lo = 0, hi = G;
+        while (hi - lo > 1) {
+            uint64_t mid = (lo + hi) / 2;
+            if (k[mid] >= key) lo = mid; else hi = mid;
+        }
+        term_group[i] = lo;
+    }
+    free(k);
+    return G;
+}
+
+static uint32_t max_exp(uint32_t n, uint64_t s, const uint32_t *exps, uint32_t j)
+{
+    uint32_t m = 0;
+    for (uint64_t i = 0; i < s; ++i)
+        if (exps[i * n + j] > m) m = exps[i * n + j];
+    return m;
+}
+
+/* --------------------------------------------------------- O1: direct ---- */
+
+int oracle_eval_direct(uint64_t p, uint32_t n, uint64_t s, const uint64_t *coeffs,
+                       const uint32_t *exps, const uint64_t *beta, uint64_t T, uint64_t t0,
+                       uint64_t G, const uint64_t *term_group, uint64_t *out)
+{
+    if (p < 2 || n < 2) return 1;
+    uint32_t E = n - 2, dmax = 0;
+    for (uint32_t j = 0; j < E; ++j) {
+        uint32_t d = max_exp(n, s, exps, 2 + j);
+        if (d > dmax) dmax = d;
+    }
+    uint64_t *pw = (uint64_t *)malloc((size_t)(E ? E : 1) * (dmax + 1) * sizeof(uint64_t));
+    memset(out, 0, (size_t)T * G * sizeof(uint64_t));
+    for (uint64_t r = 0; r < T; ++r) {
+        uint64_t t = t0 + r;
+        for (uint32_t j = 0; j < E; ++j) {            /* (beta_j^t)^e, e = 0..dmax */
+            uint64_t gam = oracle_powmod(beta[j], t, p);
+            pw[(size_t)j * (dmax + 1)] = 1 % p;
+            for (uint32_t e = 1; e <= dmax; ++e)
+                pw[(size_t)j * (dmax + 1) + e] = oracle_mulmod(pw[(size_t)j * (dmax + 1) + e - 1], gam, p);
+        }
+        uint64_t *row = out + r * G;
+        for (uint64_t i = 0; i < s; ++i) {
+            uint64_t v = coeffs[i] % p;
+            for (uint32_t j = 0; j < E; ++j)
+                v = oracle_mulmod(v, pw[(size_t)j * (dmax + 1) + exps[i * n + 2 + j]], p);
+            row[term_group[i]] = oracle_addmod(row[term_group[i]], v, p);
+        }
+    }
+    free(pw);
+    return 0;
+}
+
+/* The same definition for individual cells (t, g); `t` is the absolute point index. */
+int oracle_eval_cells(uint64_t p, uint32_t n, uint64_t s, const uint64_t *coeffs,
+                      const uint32_t *exps, const uint64_t *beta, uint64_t G,
+                      const uint64_t *term_group, uint64_t ncells, const uint64_t *cell_t,
+                      const uint64_t *cell_g, uint64_t *vals)
+{
+    if (p < 2 || n < 2) return 1;
+    uint32_t E = n - 2;
+    /* CSR of terms by group */
+    uint64_t *cnt = (uint64_t *)calloc(G + 1, sizeof(uint64_t));
+    uint64_t *idx = (uint64_t *)malloc((s ? s : 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < s; ++i) cnt[term_group[i] + 1]++;
+    for (uint64_t g = 0; g < G; ++g) cnt[g + 1] += cnt[g];
+    uint64_t *fill = (uint64_t *)malloc((G + 1) * sizeof(uint64_t));
+    memcpy(fill, cnt, (G + 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < s; ++i) idx[fill[term_group[i]]++] = i;
+    uint64_t *gam = (uint64_t *)malloc((E ? E : 1) * sizeof(uint64_t));
+    for (uint64_t c = 0; c < ncells; ++c) {
+        uint64_t t = cell_t[c], g = cell_g[c], acc = 0;
+        if (g >= G) { vals[c] = ~(uint64_t)0; continue; }
+        for (uint32_t j = 0; j < E; ++j) gam[j] = oracle_powmod(beta[j], t, p);
+        for (uint64_t q = cnt[g]; q < cnt[g + 1]; ++q) {
+            uint64_t i = idx[q], v = coeffs[i] % p;
+            for (uint32_t j = 0; j < E; ++j)
+                v = oracle_mulmod(v, oracle_powmod(gam[j], exps[i * n + 2 + j], p), p);
+            acc = oracle_addmod(acc, v, p);
+        }
+        vals[c] = acc;
+    }
+    free(cnt); free(idx); free(fill); free(gam);
+    return 0;
+}
+
+/* ------------------------------------------------- O2: Algorithm 1 ---- */
+
+/*
+ * The matrix method: power tables [beta_k^i, 0 <= i <= d_k] (Sect. 2.3), the
+ * monomial values m_i = M_i(beta) with n-3 products each, then for every
+ * point a_i <- a_i (x) m_i and c <- c (+) a_i over each run of terms with the
+ * same (d_i, e_i) (Algorithm 1).  Terms are visited in group order; the run
+ * for group g is the list of its terms.  Requires t0 >= 1: the state before
+ * the first point is a_i * m_i^(t0-1).
+ */
+int oracle_eval_matrix(uint64_t p, uint32_t n, uint64_t s, const uint64_t *coeffs,
+                       const uint32_t *exps, const uint64_t *beta, uint64_t T, uint64_t t0,
+                       uint64_t G, const uint64_t *term_group, uint64_t *out)
+{
+    if (p < 2 || n < 2 || t0 < 1) return 1;
+    uint32_t E = n - 2;
+    uint64_t *m = (uint64_t *)malloc((s ? s : 1) * sizeof(uint64_t));
+    uint64_t *a = (uint64_t *)malloc((s ? s : 1) * sizeof(uint64_t));
+    uint64_t *order = (uint64_t *)malloc((s ? s : 1) * sizeof(uint64_t));
+    uint64_t *start = (uint64_t *)calloc(G + 1, sizeof(uint64_t));
+    /* group runs (terms of group g are order[start[g] .. start[g+1])) */
+    for (uint64_t i = 0; i < s; ++i) start[term_group[i] + 1]++;
+    for (uint64_t g = 0; g < G; ++g) start[g + 1] += start[g];
+    uint64_t *fill = (uint64_t *)malloc((G + 1) * sizeof(uint64_t));
+    memcpy(fill, start, (G + 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < s; ++i) order[fill[term_group[i]]++] = i;
+    free(fill);
+    /* power tables */
+    uint32_t *deg = (uint32_t *)malloc((E ? E : 1) * sizeof(uint32_t));
+    size_t tab_sz = 0;
+    for (uint32_t j = 0; j < E; ++j) { deg[j] = max_exp(n, s, exps, 2 + j); tab_sz += deg[j] + 1; }
+    uint64_t *tab = (uint64_t *)malloc((tab_sz ? tab_sz : 1) * sizeof(uint64_t));
+    uint64_t **row = (uint64_t **)malloc((E ? E : 1) * sizeof(uint64_t *));
+    size_t off = 0;
+    for (uint32_t j = 0; j < E; ++j) {
+        row[j] = tab + off;
+        row[j][0] = 1 % p;
+        for (uint32_t e = 1; e <= deg[j]; ++e) row[j][e] = oracle_mulmod(row[j][e - 1], beta[j], p);
+        off += deg[j] + 1;
+    }
+    /* m_i = M_i(beta) and the starting state a_i * m_i^(t0-1) */
+    for (uint64_t k = 0; k < s; ++k) {
+        uint64_t i = order[k], mi = 1 % p;
+        for (uint32_t j = 0; j < E; ++j) mi = oracle_mulmod(mi, row[j][exps[i * n + 2 + j]], p);
+        m[k] = mi;
+        a[k] = oracle_mulmod(coeffs[i] % p, oracle_powmod(mi, t0 - 1, p), p);
+    }
+    /* Algorithm 1 */
+    for (uint64_t r = 0; r < T; ++r) {
+        for (uint64_t g = 0; g < G; ++g) {
+            uint64_t c = 0;
+            for (uint64_t k = start[g]; k < start[g + 1]; ++k) {
+                a[k] = oracle_mulmod(a[k], m[k], p);
+                c = oracle_addmod(c, a[k], p);
+            }
+            out[r * G + g] = c;
+        }
+    }
+    free(m); free(a); free(order); free(start); free(deg); free(tab); free(row);
+    return 0;
+}

@@ -1,0 +1,68 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle.c (on the CPU), compiles it
+and runs the pin checks against it: brute force with exact integers, Fermat's
+little theorem, the t0 = 0 coefficient sums and the paper's gcd example.  A
+mutant that every pin accepts would mean the pins are too weak.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import brute
+import workloads as wl
+
+MUTANTS = {
+    "dropped coefficient": ("uint64_t v = coeffs[i] % p;\n            for (uint32_t j = 0; j < E; ++j)\n                v = oracle_mulmod(v, pw",
+                            "uint64_t v = 1 % p;\n            for (uint32_t j = 0; j < E; ++j)\n                v = oracle_mulmod(v, pw"),
+    "wrong exponent column": ("pw[(size_t)j * (dmax + 1) + exps[i * n + 2 + j]]",
+                              "pw[(size_t)j * (dmax + 1) + exps[i * n + 1 + j]]"),
+    "off-by-one point": ("uint64_t gam = oracle_powmod(beta[j], t, p);",
+                         "uint64_t gam = oracle_powmod(beta[j], t + 1, p);"),
+    "addmod boundary": ("return s >= p ? s - p : s;", "return s > p ? s - p : s;"),
+    "ascending group order": ("return x < y ? 1 : (x > y ? -1 : 0);", "return x < y ? -1 : (x > y ? 1 : 0);"),
+    "transposed power operand": ("= oracle_mulmod(pw[(size_t)j * (dmax + 1) + e - 1], gam, p);",
+                                 "= oracle_mulmod(pw[(size_t)j * (dmax + 1) + e - 1], beta[j], p);"),
+    "powmod skips the top bit": ("while (e) {", "while (e > 1) {"),
+    "wrong beta index": ("oracle_powmod(beta[j], t, p);", "oracle_powmod(beta[E - 1 - j], t, p);"),
+}
+
+
+def _pins_hold(lib) -> bool:
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        for p in (101, 2**61 - 1):
+            rnd = random.Random(p)
+            for _ in range(20):
+                a = rnd.randrange(1, p)
+                if oracle.powmod(a, p - 1, p) != 1:
+                    return False
+            for seed in range(6):
+                r = random.Random(seed)
+                n = r.randint(3, 5)
+                w = wl.make_uniform(n=n, s=r.randint(2, 30), p=p, deg12=2, deg_rest=3, T=4, seed=seed,
+                                    sort=False)
+                for t0 in (0, 1):
+                    keys, out = oracle.eval_direct(w, t0=t0)
+                    bk, rows = brute.eval_exact(p, w.coeffs, w.exps, w.beta, w.T, t0)
+                    if [tuple(k) for k in keys.tolist()] != bk or out.tolist() != rows:
+                        return False
+        return True
+    finally:
+        oracle._lib = saved
+
+
+def test_unmutated_oracle_passes_pins():
+    assert _pins_hold(oracle._load())
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = oracle.source()
+    assert src.count(old) >= 1, name
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "mut.so"))
+    assert not _pins_hold(lib), f"pins accepted the planted mistake: {name}"
