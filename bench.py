@@ -1,0 +1,295 @@
+#!/usr/bin/env python3
+"""Benchmark of partial modular polynomial evaluation on GB300.
+
+One step = one poly_eval_run over the whole hot path (power tables, Step A,
+Step B) for the large workload: n=9, a 62-bit prime, 1e6 terms in 5,041
+(x1,x2) groups with Zipf(1.1) sizes, x3..x9 exponents in 0..20, T=1024 points.
+The metric is term-point evaluations per second (s*T per step).
+
+  value    device time of K steps with the terms resident in HBM (CUDA events
+           on the launch stream; L2 flushed by a 256 MB write between steps)
+  e2e      the same metric through the C ABI with host buffers: create from
+           host arrays (upload), run into pinned host memory (download), destroy
+  roofline Step B, timed live with events on its stream, against the integer
+           multiply issue rate of the SMs at the sampled SM clock
+  cpu_baseline  the oracle's Algorithm 1 (single thread) on a sample of groups
+
+--impl reference times the oracle instead (the method's plain CPU statement).
+Under torchrun each rank evaluates its own block of T points (weak scaling,
+no data-path collective).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+# 32-bit integer multiplies per term-point of the modular product (a 64x64
+# low product is 3, a high product 4, a full 128-bit product 4).
+MUL32_PER_TP = {"barrett64": 10, "mont64": 11}
+INT_MUL_PER_SM_PER_CLK = 64   # 32-bit IMAD issue rate per SM (CUDA throughput table)
+NUM_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="large", choices=["large", "tiny", "width62", "width50"])
+    ap.add_argument("--variant", default="auto")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-stride", type=int, default=2)
+    return ap.parse_args()
+
+
+def make_workload(name):
+    if name == "large":
+        return wl.config_large()
+    if name == "tiny":
+        return wl.config_tiny()
+    if name == "width62":
+        return wl.config_width(62)
+    return wl.config_width(50)
+
+
+def workload_config(w, name, variant, extra=None):
+    cfg = {"workload": w.name, "terms": w.s, "n": w.n, "T": int(w.T), "prime_bits": int(w.p).bit_length(),
+           "variant": variant, "config": name,
+           "l2": "flushed between timed steps by a 256 MB device write"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(w, stride):
+    """Oracle Algorithm 1 (one thread) on every `stride`-th group, all T points."""
+    import oracle
+    keys, tg = oracle.group_keys(w.exps)
+    sel = (tg % stride) == 0
+    sub = wl.Workload(p=w.p, n=w.n, coeffs=w.coeffs[sel], exps=w.exps[sel], beta=w.beta, T=w.T, t0=w.t0)
+    t = time.perf_counter()
+    oracle.eval_matrix(sub)
+    dt = time.perf_counter() - t
+    return {"value": sub.term_points / dt, "unit": "term-points/s", "cores": 1, "kind": "oracle",
+            "sample": f"Algorithm 1 of the oracle (gcc -O2, unsigned __int128) on every {stride}-th group: "
+                      f"{sub.s} terms x {w.T} points = {sub.term_points:.3e} term-points in {dt:.1f} s",
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    w = make_workload(args.config)
+    stride = max(args.cpu_sample_stride, 1) * 8
+    for _ in range(args.warmup):
+        cpu_baseline(w, stride * 8)       # untimed warm-up on a smaller sample
+    vals, secs = [], []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(w, stride)
+        vals.append(cb["value"])
+        secs.append(cb["seconds"])
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": "term-point evaluations/s", "value": value, "unit": "term-points/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload_config(w, args.config, "oracle"),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": value,
+                             "unit": "term-points/s"},
+            "e2e": {"value": value, "unit": "term-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2004_11571_gb300 as pe
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = make_workload(args.config)
+    variant = args.variant
+    if variant == "auto" and args.config == "width50":
+        variant = "fp64"
+    t0 = w.t0 + rank * w.T            # each rank: its own block of T points
+    poly = pe.Poly.from_workload(w, variant=variant)
+    G, T, s = poly.G, int(w.T), w.s
+    out = torch.empty((T, G), dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 0)):
+        poly.run(w.beta, T, t0, out=out, stream=stream)
+        flush.zero_()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    poly.set_timing(True)
+    poly.kernel_times()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        poly.run(w.beta, T, t0, out=out, stream=stream)
+        b.record(stream)
+    barrier()
+    clk = clocks.stop()
+    poly.set_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    t_pt, t_a, t_b, runs = poly.kernel_times()
+    tot = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    max_total_ms = float(tot.item())
+    value = s * T * world * args.steps / (max_total_ms * 1e-3)
+    plan = poly.plan_info(T)
+    launches = poly.launches_per_run(T) * args.steps
+
+    # End to end through the C ABI with host buffers.
+    host_out = torch.empty((T, G), dtype=torch.int64, pin_memory=True).numpy()
+    e2e_t = []
+    h2d = s * 8 + s * (w.n - 2) * (1 if int(w.exps[:, 2:].max(initial=0)) <= 255 else 2)
+    for _ in range(max(args.e2e_steps, 1)):
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
+        p2 = pe.Poly(w.p, w.coeffs, w.exps, variant=variant, sorted_hint=True)
+        p2.run(w.beta, T, t0, out=host_out)
+        p2.close()
+        e2e_t.append(time.perf_counter() - t_start)
+    e2e_val = s * T / statistics.median(e2e_t)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    # Roofline of Step B: integer-multiply issue rate at the sampled SM clock.
+    vkey = "mont64" if variant == "mont64" else "barrett64"
+    tps_b = s * T / (t_b / runs * 1e-3) if runs and t_b > 0 else None
+    mhz = clk["sm_mhz"] or 1920.0
+    roof = None
+    if variant != "fp64" and tps_b:
+        peak = NUM_SMS * INT_MUL_PER_SM_PER_CLK * mhz * 1e6 / 1e9
+        ach = tps_b * MUL32_PER_TP[vkey] / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gmul32/s", "frac": ach / peak,
+                "traffic": None, "kernel": "pe::k_stepB",
+                "peak_source": f"{NUM_SMS} SMs x {INT_MUL_PER_SM_PER_CLK} int32 mul/clk x {mhz:.0f} MHz "
+                               "(median sampled SM clock)",
+                "algorithmic": f"{MUL32_PER_TP[vkey]} 32-bit multiplies per term-point x {s}x{T} term-points",
+                "stepB_ms": t_b / runs, "stepB_term_points_per_s": tps_b}
+        try:
+            cal, cal_mhz = pe.modmul_peak(vkey, w.p)
+            roof["calibration"] = {"register_only_term_points_per_s": cal, "frac_of_register_only": tps_b / cal,
+                                   "sm_mhz_in_kernel": cal_mhz}
+        except Exception as ex:  # pragma: no cover
+            roof["calibration"] = {"error": str(ex)}
+    elif tps_b:
+        roof = {"bound": "alu", "achieved": tps_b / 1e9, "peak": None, "unit": "Gtp/s", "frac": None,
+                "traffic": None, "kernel": "pe::k_stepB", "stepB_ms": t_b / runs}
+    line = {"metric": "term-point evaluations/s", "value": value, "unit": "term-points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": workload_config(w, args.config, variant, {"groups": G, "tiles": plan,
+                                                               "per_rank_points": f"t0 + rank*{T}"}),
+            "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": "term-points/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(T * G * 8), "median_s": statistics.median(e2e_t)},
+            "gpu_launches": launches,
+            "kernel_ms_per_step": {"power_tables": t_pt / max(runs, 1), "stepA": t_a / max(runs, 1),
+                                   "stepB": t_b / max(runs, 1)},
+            "roofline": roof}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_stride)
+    print(json.dumps(line), flush=True)
+    poly.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

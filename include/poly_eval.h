@@ -1,0 +1,291 @@
+/*
+ * poly_eval.h -- C ABI of the GB300 (sm_103a) partial modular polynomial
+ * evaluation library.
+ *
+ * Problem (paper Sect. 2.1 and Sect. 2.3, Eq. 1): a prime p, a polynomial
+ *     f = sum_{i=1..s} a_i x1^{d_i} x2^{e_i} M_i(x3, ..., xn)  over F_p,
+ * a base point beta = (beta_3, ..., beta_n) in F_p^{n-2} and T points.  The
+ * library computes the T bivariate images
+ *     b_t(x1, x2) = f(x1, x2, beta^t),   t = t0, t0+1, ..., t0+T-1,
+ * by the matrix method (Sect. 2.3, Algorithm 1): monomial values
+ * m_i = M_i(beta) from per-variable power tables (Step A), then T rounds of
+ * v_i <- v_i * m_i mod p with a segmented sum over each (x1, x2) group
+ * (Step B, the "coefficient reductions").
+ *
+ * Output layout: a dense row-major T x G array of uint64, row r holding image
+ * b_{t0+r}; column g is the g-th distinct (d, e) pair in descending
+ * lexicographic order (Sect. 2.3: lex order with x1 > x2 > ...).  Every value
+ * is canonical, in [0, p).  Zero coefficients are kept (Algorithm 1 skips
+ * them; the dense layout does not).
+ *
+ * Conventions common to every call:
+ *  - p is a run-time value, never a compile-time constant (Sect. 3.1 footnote).
+ *  - Primality of p is the caller's contract; the library checks its width
+ *    and parity only.
+ *  - The input is a list of terms: repeated monomials are allowed (the images
+ *    are linear in the terms) and zero coefficients are accepted.
+ *  - Streams are passed as `void*` holding a cudaStream_t (NULL = legacy
+ *    default stream).
+ *  - No call ever falls back to a CPU computation.  Errors are returned as a
+ *    pe_status; poly_eval_last_error() gives a message for the calling thread.
+ *  - All handles are owned by the library and freed by their destroy call.
+ */
+#ifndef POLY_EVAL_H
+#define POLY_EVAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PE_OK = 0,
+    PE_ERR_ARG = 1,           /* a null pointer, a size out of range, beta_j not in [1, p) */
+    PE_ERR_PRIME = 2,         /* p even, below 3, or too wide for the chosen modular product */
+    PE_ERR_NOT_REDUCED = 3,   /* a coefficient a_i >= p */
+    PE_ERR_EXP_RANGE = 4,     /* an exponent above 65535 */
+    PE_ERR_NOMEM = 5,         /* device or host allocation failed */
+    PE_ERR_ADMISSION = 6,     /* server: request larger than the memory cap, or queue full */
+    PE_ERR_CUDA = 7,          /* a CUDA runtime error (message in poly_eval_last_error) */
+    PE_ERR_TIMEOUT = 8,       /* server poll: not finished within the timeout */
+    PE_PENDING = 9,           /* server poll with zero timeout: still running */
+    PE_ERR_NOT_FOUND = 10     /* server: unknown ticket or resident polynomial */
+} pe_status;
+
+/*
+ * Modular product used in Step B (the T x s Hadamard products).
+ *   PE_MODMUL_BARRETT64: Barrett's product (Sect. 3.1) specialised to a fixed
+ *       multiplier: per term the quotient floor(m_i 2^64 / p) is precomputed,
+ *       so v*m_i mod p costs one high and two low 64-bit products.  p odd,
+ *       3 <= p < 2^62.
+ *   PE_MODMUL_MONT64: Montgomery reduction (Sect. 3.1) with R = 2^64, m_i kept
+ *       in Montgomery form.  p odd, 3 <= p < 2^62.
+ *   PE_MODMUL_FP64: the floating-point FMA product of Algorithm 2 and the
+ *       addition of Algorithm 3, in IEEE binary64.  p odd, 3 <= p < 2^50.
+ *   PE_MODMUL_AUTO: BARRETT64 (the fastest on this GPU for every width).
+ * All variants give identical, canonical results.
+ */
+typedef enum {
+    PE_MODMUL_AUTO = 0,
+    PE_MODMUL_MONT64 = 1,
+    PE_MODMUL_FP64 = 2,
+    PE_MODMUL_BARRETT64 = 3
+} pe_variant;
+
+/* pe_poly_desc.flags */
+#define PE_FLAG_DEVICE_PTRS 0x1u  /* coeffs and exps are device pointers */
+#define PE_FLAG_SORTED      0x2u  /* hint: terms already in descending (d, e) order */
+
+#define PE_MAX_VARS 66            /* n <= 66, i.e. at most 64 evaluated variables */
+
+/*
+ * A polynomial in term-list form (Eq. 1).
+ *   p        : the prime modulus.
+ *   n        : number of variables x1..xn, 2 <= n <= PE_MAX_VARS.
+ *   exp_bytes: width of one exponent in `exps`: 1 (uint8), 2 (uint16) or 4 (uint32).
+ *   s        : number of terms (0 allowed).
+ *   coeffs   : s values a_i, each < p.
+ *   exps     : s x n exponents, row-major: exps[i*n + 0] = d_i (x1),
+ *              exps[i*n + 1] = e_i (x2), exps[i*n + k-1] = exponent of x_k.
+ *   flags    : PE_FLAG_* bits.
+ *   variant  : modular product used by poly_eval_run.
+ * The descriptor and the arrays are read during the create call only.
+ */
+typedef struct {
+    uint64_t p;
+    uint32_t n;
+    uint32_t exp_bytes;
+    uint64_t s;
+    const uint64_t *coeffs;
+    const void *exps;
+    uint32_t flags;
+    pe_variant variant;
+} pe_poly_desc;
+
+typedef struct pe_poly pe_poly;
+
+/*
+ * Validates the terms, groups them by (d, e) (a stable sort into descending
+ * lexicographic order unless they already are, Sect. 2.3), packs them into a
+ * structure-of-arrays layout and copies them to the current CUDA device.
+ * The returned handle owns that device memory until poly_eval_destroy.
+ * Errors: PE_ERR_ARG, PE_ERR_PRIME, PE_ERR_NOT_REDUCED, PE_ERR_EXP_RANGE,
+ * PE_ERR_NOMEM, PE_ERR_CUDA.  On error *out is set to NULL.
+ */
+pe_status poly_eval_create(const pe_poly_desc *desc, pe_poly **out);
+
+/*
+ * Number of nonempty (x1, x2) groups G and, if keys != NULL, their (d, e)
+ * pairs in column order: keys[2g] = d, keys[2g+1] = e (host array of 2G).
+ */
+pe_status poly_eval_groups(const pe_poly *poly, uint64_t *G, uint32_t *keys);
+
+/*
+ * Evaluates the T bivariate images b_t = f(x1, x2, beta^t), t = t0..t0+T-1
+ * (Sect. 2.1; t0 = 1 avoids the unlucky point beta^0, t0 = 0 is allowed).
+ *   beta : host array of n-2 values, each in [1, p).
+ *   out  : T x G uint64 (layout above), host or device memory.  With a device
+ *          pointer the call is asynchronous on `stream`; with a host pointer it
+ *          copies the result back and returns after the stream has finished.
+ * Runs Step A (power tables, monomial values) and Step B (Hadamard products
+ * and coefficient reductions) as CUDA kernels.  Scratch device memory is owned
+ * by the handle and reused by later calls; calls on one handle must not
+ * overlap in time.
+ */
+pe_status poly_eval_run(pe_poly *poly, const uint64_t *beta, uint64_t T, uint64_t t0,
+                        uint64_t *out, void *stream);
+
+/* Frees the handle and its device memory (NULL is a no-op). */
+void poly_eval_destroy(pe_poly *poly);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *poly_eval_last_error(void);
+
+/*
+ * Tile shape of Step B.  A warp-lane owns a chunk of at most K consecutive
+ * terms of one group and keeps their state in registers across a range of
+ * points (the paper's dependent evaluations T_d, Sect. 4.1); 32 chunks form a
+ * slab; a work item is `slabs` consecutive slabs over `tchunk` consecutive
+ * points.  Zero fields mean "choose automatically".
+ */
+typedef struct {
+    uint32_t K;               /* terms per lane: 1, 2, 4, 8 or 16 */
+    uint32_t slabs;           /* slabs per work item */
+    uint32_t tchunk;          /* points per work item */
+    uint32_t warps_per_block; /* 1..8 */
+} pe_tiles;
+
+/* Forces tile parameters for later runs of this handle (NULL = automatic). */
+pe_status poly_eval_set_tiles(pe_poly *poly, const pe_tiles *tiles);
+
+/* Tile parameters chosen for a run with T points, and the work decomposition. */
+typedef struct {
+    pe_tiles tiles;
+    pe_variant variant;
+    uint64_t chunks;          /* lane chunks (padded K-term pieces of groups) */
+    uint64_t items;           /* warp work items per run */
+    uint64_t spans;           /* groups whose terms cross work-item boundaries */
+    uint64_t padded_terms;    /* chunks * K */
+} pe_plan_info;
+
+pe_status poly_eval_plan_info(pe_poly *poly, uint64_t T, pe_plan_info *info);
+
+/*
+ * Kernel timing of later poly_eval_run calls: with timing enabled, each run
+ * records CUDA events on its launch stream around every kernel.
+ * poly_eval_kernel_times waits for the recorded runs, returns the summed
+ * durations in milliseconds -- ms[0] power tables, ms[1] Step A, ms[2] Step B --
+ * and the number of runs, then starts a new sum.
+ */
+pe_status poly_eval_set_timing(pe_poly *poly, int enable);
+pe_status poly_eval_kernel_times(pe_poly *poly, double ms[3], uint64_t *runs);
+
+/* Number of kernel launches one poly_eval_run issues (for launch accounting). */
+pe_status poly_eval_launches_per_run(pe_poly *poly, uint64_t T, uint32_t *launches);
+
+/* -------------------------------------------------------------------------
+ * Batched evaluation: many polynomials, each with its own beta, T, t0 and
+ * prime, evaluated by one persistent kernel with a device-side work queue.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    pe_poly *poly;
+    const uint64_t *beta;     /* host, n-2 values in [1, p) */
+    uint64_t T;
+    uint64_t t0;
+    uint64_t *out;            /* device, T x G */
+} pe_job;
+
+typedef struct pe_batch pe_batch;
+
+/*
+ * Plans a batch: per-job tiles (from the autotuner cache when present),
+ * a work queue ordered by decreasing cost, and a CUDA graph of the batch
+ * (power tables for every job, then one persistent kernel that runs Step A
+ * fused into Step B for every work item).  Job descriptors are copied.
+ */
+pe_status poly_eval_batch_plan(const pe_job *jobs, size_t njobs, pe_batch **out);
+
+/* Launches the planned batch's CUDA graph on `stream` (asynchronous). */
+pe_status poly_eval_batch_launch(pe_batch *batch, void *stream);
+
+/* Replaces the beta values of job `j` for later launches (same T and t0). */
+pe_status poly_eval_batch_set_beta(pe_batch *batch, size_t j, const uint64_t *beta);
+
+void poly_eval_batch_destroy(pe_batch *batch);
+
+/* One-shot convenience: plan, launch on `stream`, synchronize, destroy. */
+pe_status poly_eval_batch(const pe_job *jobs, size_t njobs, void *stream);
+
+/* -------------------------------------------------------------------------
+ * Autotuner: times candidate tile shapes for a polynomial on the current
+ * device and records the fastest under a shape bucket; later plans of any
+ * polynomial in the same bucket use it.
+ * ---------------------------------------------------------------------- */
+pe_status poly_eval_tune(pe_poly *poly, uint64_t T, pe_tiles *best, double *best_ms);
+pe_status poly_eval_tune_save(const char *path);   /* JSON lines */
+pe_status poly_eval_tune_load(const char *path);
+
+/* -------------------------------------------------------------------------
+ * Server: continuous batching of evaluation requests.  Requests are
+ * admitted by device memory, polynomials can stay resident across
+ * requests, and admitted jobs are packed into persistent-kernel epochs
+ * that overlap on two streams.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    uint64_t mem_cap_bytes;   /* cap on resident terms + scratch + outputs */
+    uint32_t max_queue;       /* pending requests before PE_ERR_ADMISSION */
+    uint32_t max_epoch_jobs;  /* jobs packed into one epoch */
+    uint32_t streams;         /* epochs in flight (1..4) */
+} pe_server_cfg;
+
+typedef struct pe_server pe_server;
+
+/*
+ * One request.  Exactly one of `poly_desc` (a new polynomial, uploaded by the
+ * server) and `resident_id` (a polynomial registered with
+ * poly_eval_server_register, reused at a new beta) is used: resident_id = 0
+ * selects poly_desc.  `out` is a host buffer of T x G uint64 that must stay
+ * valid until the ticket completes.
+ */
+typedef struct {
+    const pe_poly_desc *poly_desc;
+    uint64_t resident_id;
+    const uint64_t *beta;
+    uint64_t T;
+    uint64_t t0;
+    uint64_t *out;
+} pe_request;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, epochs;
+    double p50_ms, p99_ms, max_ms;      /* submit-to-completion latency */
+    double term_points;                 /* sum of s*T over completed requests */
+    double busy_s;                      /* wall time with at least one epoch in flight */
+    uint64_t resident_bytes, resident_polys, evictions;
+} pe_server_stats;
+
+pe_status poly_eval_server_create(const pe_server_cfg *cfg, pe_server **out);
+/* Uploads a polynomial into the resident store; returns its id (> 0). */
+pe_status poly_eval_server_register(pe_server *srv, const pe_poly_desc *desc, uint64_t *resident_id);
+/* Queues a request; PE_ERR_ADMISSION is backpressure (queue full or too large). */
+pe_status poly_eval_server_submit(pe_server *srv, const pe_request *req, uint64_t *ticket);
+/* PE_OK when done (result in req->out), PE_PENDING / PE_ERR_TIMEOUT otherwise. */
+pe_status poly_eval_server_poll(pe_server *srv, uint64_t ticket, int64_t timeout_us);
+pe_status poly_eval_server_stats(pe_server *srv, pe_server_stats *stats);
+void poly_eval_server_destroy(pe_server *srv);
+
+/* -------------------------------------------------------------------------
+ * Roofline calibration: a register-only kernel that runs the Step B inner
+ * operation (one modular product and one modular addition per term-point,
+ * Algorithm 1) on independent chains at full occupancy; returns its rate in
+ * term-points per second and the SM clock seen by the kernel.
+ * ---------------------------------------------------------------------- */
+pe_status poly_eval_modmul_peak(pe_variant variant, uint64_t p, double *term_points_per_s,
+                                double *sm_clock_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLY_EVAL_H */

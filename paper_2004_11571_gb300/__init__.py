@@ -1,0 +1,288 @@
+"""Python binding of libpolyeval (partial modular polynomial evaluation on GB300).
+
+Argument marshalling only: every step of the evaluation runs in the library's
+CUDA kernels.  PyTorch supplies device buffers and streams.  If the compiled
+library is missing the import of any entry point raises; there is no CPU
+fallback.
+
+Entry points mirror include/poly_eval.h:
+  Poly(p, coeffs, exps, variant)        poly_eval_create
+  Poly.groups() / Poly.G                poly_eval_groups
+  Poly.run(beta, T, t0, out, stream)    poly_eval_run
+  Poly.set_tiles / Poly.plan_info       poly_eval_set_tiles / poly_eval_plan_info
+  Batch(jobs) / Batch.launch            poly_eval_batch_plan / _launch
+  tune(poly, T)                         poly_eval_tune
+  Server(...)                           poly_eval_server_*
+  modmul_peak(variant, p)               poly_eval_modmul_peak
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpolyeval.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "poly_eval.h")
+
+VARIANTS = {"auto": 0, "mont64": 1, "fp64": 2, "barrett64": 3}
+STATUS = {0: "PE_OK", 1: "PE_ERR_ARG", 2: "PE_ERR_PRIME", 3: "PE_ERR_NOT_REDUCED", 4: "PE_ERR_EXP_RANGE",
+          5: "PE_ERR_NOMEM", 6: "PE_ERR_ADMISSION", 7: "PE_ERR_CUDA", 8: "PE_ERR_TIMEOUT", 9: "PE_PENDING",
+          10: "PE_ERR_NOT_FOUND"}
+PE_OK, PE_PENDING, PE_ERR_TIMEOUT, PE_ERR_ADMISSION = 0, 9, 8, 6
+FLAG_DEVICE_PTRS, FLAG_SORTED = 0x1, 0x2
+
+
+class PolyEvalError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_uint64), ("n", ctypes.c_uint32), ("exp_bytes", ctypes.c_uint32),
+                ("s", ctypes.c_uint64), ("coeffs", ctypes.c_void_p), ("exps", ctypes.c_void_p),
+                ("flags", ctypes.c_uint32), ("variant", ctypes.c_int)]
+
+
+class _Tiles(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_uint32), ("slabs", ctypes.c_uint32), ("tchunk", ctypes.c_uint32),
+                ("warps_per_block", ctypes.c_uint32)]
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [("tiles", _Tiles), ("variant", ctypes.c_int), ("chunks", ctypes.c_uint64),
+                ("items", ctypes.c_uint64), ("spans", ctypes.c_uint64), ("padded_terms", ctypes.c_uint64)]
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("poly", ctypes.c_void_p), ("beta", ctypes.c_void_p), ("T", ctypes.c_uint64),
+                ("t0", ctypes.c_uint64), ("out", ctypes.c_void_p)]
+
+
+class _ServerCfg(ctypes.Structure):
+    _fields_ = [("mem_cap_bytes", ctypes.c_uint64), ("max_queue", ctypes.c_uint32),
+                ("max_epoch_jobs", ctypes.c_uint32), ("streams", ctypes.c_uint32)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("poly_desc", ctypes.c_void_p), ("resident_id", ctypes.c_uint64), ("beta", ctypes.c_void_p),
+                ("T", ctypes.c_uint64), ("t0", ctypes.c_uint64), ("out", ctypes.c_void_p)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("epochs", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("term_points", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("resident_bytes", ctypes.c_uint64), ("resident_polys", ctypes.c_uint64),
+                ("evictions", ctypes.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+_vp, _u64, _u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+
+
+def declared_functions() -> list:
+    """Names of the functions declared in include/poly_eval.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(poly_eval_\w+)\s*\(", text)))
+
+
+def lib():
+    """The loaded library; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpolyeval.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        st = ctypes.c_int
+        sig = {
+            "poly_eval_create": (st, [ctypes.POINTER(_Desc), ctypes.POINTER(_vp)]),
+            "poly_eval_groups": (st, [_vp, ctypes.POINTER(_u64), _vp]),
+            "poly_eval_run": (st, [_vp, _vp, _u64, _u64, _vp, _vp]),
+            "poly_eval_destroy": (None, [_vp]),
+            "poly_eval_last_error": (ctypes.c_char_p, []),
+            "poly_eval_set_tiles": (st, [_vp, ctypes.POINTER(_Tiles)]),
+            "poly_eval_plan_info": (st, [_vp, _u64, ctypes.POINTER(_PlanInfo)]),
+            "poly_eval_launches_per_run": (st, [_vp, _u64, ctypes.POINTER(_u32)]),
+            "poly_eval_set_timing": (st, [_vp, ctypes.c_int]),
+            "poly_eval_kernel_times": (st, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64)]),
+            "poly_eval_batch_plan": (st, [_vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
+            "poly_eval_batch_launch": (st, [_vp, _vp]),
+            "poly_eval_batch_set_beta": (st, [_vp, ctypes.c_size_t, _vp]),
+            "poly_eval_batch_destroy": (None, [_vp]),
+            "poly_eval_batch": (st, [_vp, ctypes.c_size_t, _vp]),
+            "poly_eval_tune": (st, [_vp, _u64, ctypes.POINTER(_Tiles), ctypes.POINTER(ctypes.c_double)]),
+            "poly_eval_tune_save": (st, [ctypes.c_char_p]),
+            "poly_eval_tune_load": (st, [ctypes.c_char_p]),
+            "poly_eval_server_create": (st, [ctypes.POINTER(_ServerCfg), ctypes.POINTER(_vp)]),
+            "poly_eval_server_register": (st, [_vp, ctypes.POINTER(_Desc), ctypes.POINTER(_u64)]),
+            "poly_eval_server_submit": (st, [_vp, ctypes.POINTER(_Request), ctypes.POINTER(_u64)]),
+            "poly_eval_server_poll": (st, [_vp, _u64, ctypes.c_int64]),
+            "poly_eval_server_stats": (st, [_vp, ctypes.POINTER(_ServerStats)]),
+            "poly_eval_server_destroy": (None, [_vp]),
+            "poly_eval_modmul_peak": (st, [ctypes.c_int, _u64, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(status: int):
+    if status != PE_OK:
+        msg = lib().poly_eval_last_error()
+        raise PolyEvalError(status, msg.decode() if msg else "")
+
+
+def _variant(v) -> int:
+    return VARIANTS[v] if isinstance(v, str) else int(v)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _make_desc(p, coeffs, exps, variant, sorted_hint):
+    """Builds a descriptor; returns (desc, keepalive)."""
+    if _is_torch(coeffs):
+        import torch
+        if not coeffs.is_cuda:
+            coeffs = coeffs.numpy()
+            exps = exps.numpy()
+    if _is_torch(coeffs):
+        exps_t = exps.contiguous()
+        coeffs_t = coeffs.contiguous()
+        s, n = exps_t.shape
+        eb = exps_t.element_size()
+        desc = _Desc(p, n, eb, s, coeffs_t.data_ptr(), exps_t.data_ptr(),
+                     FLAG_DEVICE_PTRS | (FLAG_SORTED if sorted_hint else 0), _variant(variant))
+        return desc, (coeffs_t, exps_t)
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.uint64)
+    exps = np.asarray(exps)
+    if exps.dtype not in (np.uint8, np.uint16, np.uint32):
+        exps = exps.astype(np.uint32)
+    exps = np.ascontiguousarray(exps)
+    s = coeffs.shape[0]
+    n = exps.shape[1] if exps.ndim == 2 else 0
+    desc = _Desc(p, n, exps.dtype.itemsize, s, coeffs.ctypes.data, exps.ctypes.data,
+                 FLAG_SORTED if sorted_hint else 0, _variant(variant))
+    return desc, (coeffs, exps)
+
+
+class Poly:
+    """A polynomial resident on the current CUDA device (poly_eval_create)."""
+
+    def __init__(self, p: int, coeffs, exps, variant="auto", sorted_hint: bool = False):
+        L = lib()
+        desc, keep = _make_desc(int(p), coeffs, exps, variant, sorted_hint)
+        h = ctypes.c_void_p()
+        _check(L.poly_eval_create(ctypes.byref(desc), ctypes.byref(h)))
+        self._h = h
+        self.p = int(p)
+        self.n = int(desc.n)
+        self.s = int(desc.s)
+        G = ctypes.c_uint64()
+        _check(L.poly_eval_groups(h, ctypes.byref(G), None))
+        self.G = int(G.value)
+
+    @classmethod
+    def from_workload(cls, w, variant="auto"):
+        return cls(w.p, w.coeffs, w.exps, variant=variant)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def groups(self) -> np.ndarray:
+        keys = np.zeros((max(self.G, 1), 2), np.uint32)
+        G = ctypes.c_uint64()
+        _check(lib().poly_eval_groups(self._h, ctypes.byref(G), keys.ctypes.data))
+        return keys[: self.G].copy()
+
+    def run(self, beta: Sequence[int], T: int, t0: int = 1, out=None, stream=None):
+        """Evaluates T images; returns `out` (a new int64 CUDA tensor of shape (T, G) when None)."""
+        b = np.ascontiguousarray(np.asarray(beta, dtype=np.uint64).reshape(-1))
+        if out is None:
+            import torch
+            out = torch.empty((int(T), self.G), dtype=torch.int64, device="cuda")
+        ptr = out.data_ptr() if _is_torch(out) else out.ctypes.data
+        bptr = b.ctypes.data if b.size else None
+        _check(lib().poly_eval_run(self._h, bptr, int(T), int(t0), ptr, _stream_ptr(stream)))
+        return out
+
+    def set_tiles(self, K=0, slabs=0, tchunk=0, warps_per_block=0):
+        t = _Tiles(K, slabs, tchunk, warps_per_block)
+        _check(lib().poly_eval_set_tiles(self._h, ctypes.byref(t)))
+
+    def plan_info(self, T: int) -> dict:
+        info = _PlanInfo()
+        _check(lib().poly_eval_plan_info(self._h, int(T), ctypes.byref(info)))
+        return {"K": info.tiles.K, "slabs": info.tiles.slabs, "tchunk": info.tiles.tchunk,
+                "warps_per_block": info.tiles.warps_per_block, "variant": info.variant,
+                "chunks": info.chunks, "items": info.items, "spans": info.spans,
+                "padded_terms": info.padded_terms}
+
+    def launches_per_run(self, T: int) -> int:
+        n = ctypes.c_uint32()
+        _check(lib().poly_eval_launches_per_run(self._h, int(T), ctypes.byref(n)))
+        return int(n.value)
+
+    def set_timing(self, enable: bool = True):
+        _check(lib().poly_eval_set_timing(self._h, 1 if enable else 0))
+
+    def kernel_times(self):
+        """(ms power tables, ms Step A, ms Step B, runs) summed since the last call."""
+        ms = (ctypes.c_double * 3)()
+        runs = ctypes.c_uint64()
+        _check(lib().poly_eval_kernel_times(self._h, ms, ctypes.byref(runs)))
+        return ms[0], ms[1], ms[2], int(runs.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().poly_eval_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def modmul_peak(variant="barrett64", p: int = (1 << 61) - 1):
+    """(term-points/s, SM MHz) of the register-only Step B inner loop."""
+    tps, mhz = ctypes.c_double(), ctypes.c_double()
+    _check(lib().poly_eval_modmul_peak(_variant(variant), int(p), ctypes.byref(tps), ctypes.byref(mhz)))
+    return tps.value, mhz.value
+
+
+def to_u64(t) -> np.ndarray:
+    """A (T, G) int64 CUDA tensor or numpy array viewed as uint64 on the host."""
+    if _is_torch(t):
+        t = t.cpu().numpy()
+    return np.ascontiguousarray(t).view(np.uint64)

@@ -1,0 +1,615 @@
+// C ABI of the plain path: create / groups / run / destroy, tile planning.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <numeric>
+#include "internal.h"
+#include "kernels.h"
+
+namespace pe {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+pe_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PE_ERR_NOMEM : PE_ERR_CUDA;
+}
+
+ModCtx make_modctx(uint64_t p)
+{
+    ModCtx m{};
+    m.p = p;
+    m.p2 = 2 * p;
+    uint64_t inv = p;                           // p*p = 1 mod 8: three correct bits
+    for (int i = 0; i < 5; ++i) inv *= 2 - p * inv;  // Newton-Hensel, doubling the bits
+    m.pinv = inv;
+    m.pinv_neg = 0 - inv;
+    const unsigned __int128 R = (unsigned __int128)1 << 64;
+    m.r1 = (uint64_t)(R % p);
+    m.r2 = (uint64_t)(((unsigned __int128)m.r1 * m.r1) % p);
+    m.w64q = (uint64_t)(((unsigned __int128)m.r1 << 64) / p);
+    m.one_q = (uint64_t)(R / p);
+    m.pd = (double)p;
+    m.ud = 1.0 / (double)p;
+    return m;
+}
+
+int num_sms()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
+pe_status check_beta(const pe_poly *poly, const uint64_t *beta, BetaArg *arg)
+{
+    memset(arg, 0, sizeof *arg);
+    if (poly->E == 0) return PE_OK;
+    if (!beta) {
+        set_error("beta is NULL");
+        return PE_ERR_ARG;
+    }
+    for (uint32_t j = 0; j < poly->E; ++j) {
+        if (beta[j] == 0 || beta[j] >= poly->p) {
+            set_error("beta[%u] = %llu is not in [1, p)", j, (unsigned long long)beta[j]);
+            return PE_ERR_ARG;
+        }
+        arg->b[j] = beta[j];
+    }
+    return PE_OK;
+}
+
+static uint64_t count_chunks(const pe_poly *P, uint32_t K)
+{
+    uint64_t nc = 0;
+    for (uint64_t g = 0; g < P->G; ++g) nc += (P->group_off[g + 1] - P->group_off[g] + K - 1) / K;
+    return nc;
+}
+
+double estimate_cost(uint64_t NC, uint32_t K, uint32_t kslabs, uint64_t Tc, uint64_t T, uint64_t R)
+{
+    const uint64_t slabs = (NC + 31) / 32;
+    const uint64_t U = (slabs + kslabs - 1) / kslabs;
+    const uint64_t Q = (T + Tc - 1) / Tc;
+    const uint64_t items = U * Q;
+    const uint64_t waves = (items + R - 1) / R;
+    // Per lane and point: K products+sums (~17 instructions each) plus the
+    // transposed walk (~12).  Jump start: ~2 log2(t) Montgomery products of
+    // ~22 instructions for each of the K terms, once per slab and T-chunk.
+    const double lg = Q > 1 ? std::log2((double)T) : 0.0;
+    const double per_slab = (double)Tc * (17.0 * K + 12.0) + (Q > 1 ? 44.0 * K * lg : 4.0 * K * 22.0);
+    return (double)waves * kslabs * per_slab;
+}
+
+Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
+{
+    Tiles t;
+    t.wpb = (f && f->warps_per_block) ? f->warps_per_block : 4;
+    if (f && f->K) {
+        t.K = f->K;
+    } else {
+        // Padded slots plus the per-chunk walk: a chunk costs K products+sums
+        // and one walk entry (~0.7 of a product+sum) per point.
+        double best = 1e300;
+        for (uint32_t K : {1u, 2u, 4u, 8u}) {
+            const double nc = (double)count_chunks(P, K);
+            const double c = nc * (K + 0.7);
+            if (c < best * 0.98) {
+                best = c;
+                t.K = K;
+            }
+        }
+    }
+    const uint64_t NC = count_chunks(P, t.K);
+    int bps = 0;
+    if (stepB_occupancy((int)t.K, P->variant, (int)t.wpb, &bps) != cudaSuccess || bps <= 0) bps = 1;
+    const uint64_t R = (uint64_t)bps * t.wpb * num_sms();
+    if (f && f->slabs && f->tchunk) {
+        t.kslabs = f->slabs;
+        t.Tc = (uint32_t)std::min<uint64_t>(f->tchunk, T);
+        return t;
+    }
+    double best = 1e300;
+    const uint64_t slabs = (NC + 31) / 32;
+    const uint32_t qmax = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(64, T / 32));
+    for (uint32_t Q = 1; Q <= qmax; ++Q) {
+        const uint64_t Tc = (T + Q - 1) / Q;
+        if (f && f->tchunk && Tc != std::min<uint64_t>(f->tchunk, T)) continue;
+        for (uint32_t k = 1; k <= 64 && k <= std::max<uint64_t>(1, slabs); ++k) {
+            if (f && f->slabs && k != f->slabs) continue;
+            const double c = estimate_cost(NC, t.K, k, Tc, T, R);
+            if (c < best * 0.999) {
+                best = c;
+                t.kslabs = k;
+                t.Tc = (uint32_t)Tc;
+            }
+        }
+    }
+    if (!t.kslabs) {
+        t.kslabs = f && f->slabs ? f->slabs : 1;
+        t.Tc = (uint32_t)std::min<uint64_t>(f && f->tchunk ? f->tchunk : T, T);
+    }
+    return t;
+}
+
+static void build_chunks(pe_poly *P, uint32_t K)
+{
+    HostChunks &h = P->chunks;
+    if (h.K == K && !h.cs.empty()) return;
+    h.K = K;
+    h.cs.clear();
+    h.cg.clear();
+    h.gfirst.assign(P->G + 1, 0);
+    for (uint64_t g = 0; g < P->G; ++g) {
+        h.gfirst[g] = (uint32_t)h.cg.size();
+        for (uint64_t st = P->group_off[g]; st < P->group_off[g + 1]; st += K) {
+            h.cs.push_back((uint32_t)st);
+            h.cg.push_back((uint32_t)g);
+        }
+    }
+    h.gfirst[P->G] = (uint32_t)h.cg.size();
+    h.cs.push_back((uint32_t)P->s);
+}
+
+pe_status ensure_plan(pe_poly *P, const Tiles &t, uint64_t T)
+{
+    Plan &pl = P->plan;
+    if (pl.valid && pl.K == t.K && pl.kslabs == t.kslabs && pl.Tc == t.Tc && pl.T == T && pl.wpb == t.wpb)
+        return PE_OK;
+    pl.valid = false;
+    build_chunks(P, t.K);
+    const HostChunks &h = P->chunks;
+    const uint32_t NC = (uint32_t)h.cg.size();
+    const uint32_t per_unit = 32u * t.kslabs;
+    const uint32_t U = (NC + per_unit - 1) / per_unit;
+    const uint32_t Q = (uint32_t)((T + t.Tc - 1) / t.Tc);
+    std::vector<int32_t> unit(4 * (size_t)U, -1);   // lslot, rslot, lspan, rspan
+    std::vector<uint32_t> sg, sbase, sn;
+    uint32_t nslots = 0;
+    for (uint64_t g = 0; g < P->G; ++g) {
+        const uint32_t ua = h.gfirst[g] / per_unit, ub = (h.gfirst[g + 1] - 1) / per_unit;
+        if (ub == ua) continue;
+        const int32_t sp = (int32_t)sg.size();
+        sg.push_back((uint32_t)g);
+        sbase.push_back(nslots);
+        sn.push_back(ub - ua + 1);
+        unit[1 * (size_t)U + ua] = (int32_t)nslots;
+        unit[3 * (size_t)U + ua] = sp;
+        for (uint32_t u = ua + 1; u <= ub; ++u) {
+            unit[0 * (size_t)U + u] = (int32_t)(nslots + (u - ua));
+            unit[2 * (size_t)U + u] = sp;
+        }
+        nslots += ub - ua + 1;
+    }
+    const uint32_t S = (uint32_t)sg.size();
+    std::vector<uint32_t> span(3 * (size_t)std::max<uint32_t>(S, 1));
+    for (uint32_t i = 0; i < S; ++i) {
+        span[i] = sg[i];
+        span[S + i] = sbase[i];
+        span[2 * (size_t)S + i] = sn[i];
+    }
+    cudaError_t e;
+    if ((e = pl.cs.ensure(h.cs.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
+    if ((e = pl.cg.ensure(std::max<size_t>(h.cg.size(), 1) * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
+    if ((e = pl.unit.ensure(unit.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
+    if ((e = pl.span.ensure(span.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
+    if ((e = pl.counters.ensure((size_t)std::max<uint32_t>(S, 1) * Q * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
+    if ((e = pl.carry.ensure(nslots ? (size_t)nslots * T * 16 : 16)) != cudaSuccess) return cuda_fail(e, "carry alloc");
+    const size_t chain_bytes = t.kslabs > 1 ? (size_t)U * Q * t.Tc * 16 : 16;
+    if ((e = pl.chain.ensure(chain_bytes)) != cudaSuccess) return cuda_fail(e, "chain alloc");
+    if ((e = cudaMemcpy(pl.cs.p, h.cs.data(), h.cs.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (NC && (e = cudaMemcpy(pl.cg.p, h.cg.data(), h.cg.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(pl.unit.p, unit.data(), unit.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(pl.span.p, span.data(), span.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(pl.counters.p, 0, pl.counters.bytes)) != cudaSuccess)
+        return cuda_fail(e, "plan upload");
+    pl.K = t.K;
+    pl.kslabs = t.kslabs;
+    pl.Tc = t.Tc;
+    pl.wpb = t.wpb;
+    pl.T = T;
+    pl.NC = NC;
+    pl.U = U;
+    pl.Q = Q;
+    pl.S = S;
+    pl.nslots = nslots;
+    pl.valid = true;
+    return PE_OK;
+}
+
+StepBJob make_job(pe_poly *P, uint64_t T, uint64_t t0, uint64_t *out_dev, bool fused)
+{
+    const Plan &pl = P->plan;
+    StepBJob J{};
+    J.coeffs = P->coeffs.as<uint64_t>();
+    J.mR = fused ? nullptr : P->mR.as<uint64_t>();
+    J.exps = P->exps.p;
+    J.ptab = P->ptab.as<uint64_t>();
+    J.cs = pl.cs.as<uint32_t>();
+    J.cg = pl.cg.as<uint32_t>();
+    const int32_t *unit = pl.unit.as<int32_t>();
+    J.u_lslot = unit;
+    J.u_rslot = unit + pl.U;
+    J.u_lspan = unit + 2 * (size_t)pl.U;
+    J.u_rspan = unit + 3 * (size_t)pl.U;
+    const uint32_t S = std::max<uint32_t>(pl.S, 1);
+    J.span_g = pl.span.as<uint32_t>();
+    J.span_base = J.span_g + S;
+    J.span_n = J.span_g + 2 * (size_t)S;
+    J.counters = pl.counters.as<uint32_t>();
+    J.carry = pl.carry.as<ulonglong2>();
+    J.chain = pl.chain.as<ulonglong2>();
+    J.out = out_dev;
+    J.s = P->s;
+    J.T = T;
+    J.t0 = t0;
+    J.G = P->G;
+    J.NC = pl.NC;
+    J.U = pl.U;
+    J.Q = pl.Q;
+    J.kslabs = pl.kslabs;
+    J.Tc = pl.Tc;
+    J.E = P->E;
+    J.dp1 = P->dmax + 1;
+    J.exp_bytes = P->exp_bytes;
+    J.mc = P->mc;
+    return J;
+}
+
+static inline uint32_t read_exp(const void *exps, uint32_t width, uint64_t idx)
+{
+    switch (width) {
+    case 1: return ((const uint8_t *)exps)[idx];
+    case 2: return ((const uint16_t *)exps)[idx];
+    default: return ((const uint32_t *)exps)[idx];
+    }
+}
+
+static pe_status check_prime(uint64_t p, int variant)
+{
+    if (p < 3 || (p & 1) == 0) {
+        set_error("p = %llu must be odd and at least 3", (unsigned long long)p);
+        return PE_ERR_PRIME;
+    }
+    if (p >= (1ull << 62)) {
+        set_error("p must be below 2^62");
+        return PE_ERR_PRIME;
+    }
+    if (variant == PE_MODMUL_FP64 && p >= (1ull << 50)) {
+        set_error("the FP64 modular product (Algorithm 2) needs p < 2^50");
+        return PE_ERR_PRIME;
+    }
+    return PE_OK;
+}
+
+}  // namespace pe
+
+using namespace pe;
+
+extern "C" const char *poly_eval_last_error(void) { return g_err.c_str(); }
+
+extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return PE_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!d) {
+        set_error("desc is NULL");
+        return PE_ERR_ARG;
+    }
+    if (d->n < 2 || d->n > PE_MAX_VARS) {
+        set_error("n = %u is outside [2, %d]", d->n, PE_MAX_VARS);
+        return PE_ERR_ARG;
+    }
+    if (d->exp_bytes != 1 && d->exp_bytes != 2 && d->exp_bytes != 4) {
+        set_error("exp_bytes must be 1, 2 or 4");
+        return PE_ERR_ARG;
+    }
+    if (d->s >= 0xffffffffull) {
+        set_error("at most 2^32-2 terms");
+        return PE_ERR_ARG;
+    }
+    if (d->s && (!d->coeffs || !d->exps)) {
+        set_error("coeffs or exps is NULL");
+        return PE_ERR_ARG;
+    }
+    int variant = d->variant;
+    if (variant == PE_MODMUL_AUTO) variant = PE_MODMUL_BARRETT64;
+    if (variant != PE_MODMUL_MONT64 && variant != PE_MODMUL_FP64 && variant != PE_MODMUL_BARRETT64) {
+        set_error("unknown variant %d", (int)d->variant);
+        return PE_ERR_ARG;
+    }
+    pe_status st = check_prime(d->p, variant);
+    if (st != PE_OK) return st;
+
+    const uint64_t s = d->s;
+    const uint32_t n = d->n, E = n - 2, w = d->exp_bytes;
+    // Host views of the terms (device inputs are staged through the host).
+    std::vector<uint64_t> hc;
+    std::vector<uint8_t> he;
+    const uint64_t *coeffs = d->coeffs;
+    const void *exps = d->exps;
+    if ((d->flags & PE_FLAG_DEVICE_PTRS) && s) {
+        hc.resize(s);
+        he.resize(s * n * w);
+        cudaError_t e;
+        if ((e = cudaMemcpy(hc.data(), d->coeffs, s * 8, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(he.data(), d->exps, s * n * w, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "reading device terms");
+        coeffs = hc.data();
+        exps = he.data();
+    }
+    // Validation.
+    uint32_t dmax = 0;
+    for (uint64_t i = 0; i < s; ++i) {
+        if (coeffs[i] >= d->p) {
+            set_error("coefficient %llu of term %llu is not reduced mod p", (unsigned long long)coeffs[i],
+                      (unsigned long long)i);
+            return PE_ERR_NOT_REDUCED;
+        }
+        for (uint32_t j = 2; j < n; ++j) dmax = std::max(dmax, read_exp(exps, w, i * n + j));
+    }
+    if (dmax > 0xffff) {
+        set_error("exponent %u above 65535", dmax);
+        return PE_ERR_EXP_RANGE;
+    }
+    // Group order: descending lex on (d, e); stable sort only when needed (Sect. 2.3).
+    std::vector<uint64_t> key(s);
+    bool sorted = true;
+    for (uint64_t i = 0; i < s; ++i) {
+        key[i] = ((uint64_t)read_exp(exps, w, i * n) << 32) | read_exp(exps, w, i * n + 1);
+        if (i && key[i] > key[i - 1]) sorted = false;
+    }
+    std::vector<uint32_t> perm;
+    if (!sorted) {
+        perm.resize(s);
+        std::iota(perm.begin(), perm.end(), 0u);
+        std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return key[a] > key[b]; });
+    }
+    auto src = [&](uint64_t i) -> uint64_t { return sorted ? i : perm[i]; };
+
+    pe_poly *P = new pe_poly();
+    P->p = d->p;
+    P->n = n;
+    P->E = E;
+    P->s = s;
+    P->variant = variant;
+    P->mc = make_modctx(d->p);
+    P->dmax = dmax;
+    P->exp_bytes = dmax <= 0xff ? 1 : 2;
+    // Groups.
+    P->group_off.push_back(0);
+    for (uint64_t i = 0; i < s; ++i) {
+        const uint64_t k = key[src(i)];
+        if (i == 0 || k != key[src(i - 1)]) {
+            if (i) P->group_off.push_back(i);
+            P->keys.push_back((uint32_t)(k >> 32));
+            P->keys.push_back((uint32_t)(k & 0xffffffffu));
+        }
+    }
+    if (s) P->group_off.push_back(s);
+    P->G = P->keys.size() / 2;
+    // Structure-of-arrays packing: coefficients, then E rows of exponents.
+    std::vector<uint64_t> sc(s);
+    std::vector<uint8_t> se((size_t)E * s * P->exp_bytes);
+    for (uint64_t i = 0; i < s; ++i) {
+        const uint64_t o = src(i);
+        sc[i] = coeffs[o];
+        for (uint32_t j = 0; j < E; ++j) {
+            const uint32_t x = read_exp(exps, w, o * n + 2 + j);
+            if (P->exp_bytes == 1) se[(size_t)j * s + i] = (uint8_t)x;
+            else ((uint16_t *)se.data())[(size_t)j * s + i] = (uint16_t)x;
+        }
+    }
+    cudaError_t e;
+    const size_t dp1 = dmax + 1;
+    if ((e = P->coeffs.ensure(s * 8)) != cudaSuccess || (e = P->exps.ensure(se.size())) != cudaSuccess ||
+        (e = P->mR.ensure(s * 8)) != cudaSuccess || (e = P->ptab.ensure((size_t)E * dp1 * 8)) != cudaSuccess) {
+        delete P;
+        return cuda_fail(e, "device allocation");
+    }
+    if ((s && (e = cudaMemcpy(P->coeffs.p, sc.data(), s * 8, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (se.size() && (e = cudaMemcpy(P->exps.p, se.data(), se.size(), cudaMemcpyHostToDevice)) != cudaSuccess)) {
+        delete P;
+        return cuda_fail(e, "uploading terms");
+    }
+    *out = P;
+    return PE_OK;
+}
+
+extern "C" void poly_eval_destroy(pe_poly *P) { delete P; }
+
+extern "C" pe_status poly_eval_groups(const pe_poly *P, uint64_t *G, uint32_t *keys)
+{
+    if (!P || !G) {
+        set_error("NULL argument");
+        return PE_ERR_ARG;
+    }
+    *G = P->G;
+    if (keys && P->G) memcpy(keys, P->keys.data(), P->keys.size() * 4);
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_set_tiles(pe_poly *P, const pe_tiles *t)
+{
+    if (!P) {
+        set_error("NULL poly");
+        return PE_ERR_ARG;
+    }
+    pe_tiles z{};
+    if (!t) t = &z;
+    if (t->K && t->K != 1 && t->K != 2 && t->K != 4 && t->K != 8 && t->K != 16) {
+        set_error("K must be 1, 2, 4, 8 or 16");
+        return PE_ERR_ARG;
+    }
+    if (t->warps_per_block > 8) {
+        set_error("warps_per_block must be at most 8");
+        return PE_ERR_ARG;
+    }
+    P->forced = *t;
+    P->plan.valid = false;
+    return PE_OK;
+}
+
+static pe_status plan_for(pe_poly *P, uint64_t T, Tiles *tiles)
+{
+    *tiles = choose_tiles(P, T, &P->forced);
+    return ensure_plan(P, *tiles, T);
+}
+
+extern "C" pe_status poly_eval_plan_info(pe_poly *P, uint64_t T, pe_plan_info *info)
+{
+    if (!P || !info || T == 0) {
+        set_error("bad argument");
+        return PE_ERR_ARG;
+    }
+    Tiles t;
+    pe_status st = plan_for(P, T, &t);
+    if (st != PE_OK) return st;
+    memset(info, 0, sizeof *info);
+    info->tiles.K = t.K;
+    info->tiles.slabs = t.kslabs;
+    info->tiles.tchunk = t.Tc;
+    info->tiles.warps_per_block = t.wpb;
+    info->variant = (pe_variant)P->variant;
+    info->chunks = P->plan.NC;
+    info->items = (uint64_t)P->plan.U * P->plan.Q;
+    info->spans = P->plan.S;
+    info->padded_terms = (uint64_t)P->plan.NC * t.K;
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_set_timing(pe_poly *P, int enable)
+{
+    if (!P) {
+        set_error("NULL poly");
+        return PE_ERR_ARG;
+    }
+    P->timing = enable != 0;
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_kernel_times(pe_poly *P, double ms[3], uint64_t *runs)
+{
+    if (!P || !ms) {
+        set_error("NULL argument");
+        return PE_ERR_ARG;
+    }
+    ms[0] = ms[1] = ms[2] = 0.0;
+    const size_t nrun = P->events_used / 4;
+    for (size_t r = 0; r < nrun; ++r) {
+        cudaEvent_t *ev = &P->events[4 * r];
+        cudaError_t e = cudaEventSynchronize(ev[3]);
+        if (e != cudaSuccess) return cuda_fail(e, "timing");
+        for (int k = 0; k < 3; ++k) {
+            float x = 0.f;
+            if ((e = cudaEventElapsedTime(&x, ev[k], ev[k + 1])) != cudaSuccess) return cuda_fail(e, "timing");
+            ms[k] += x;
+        }
+    }
+    if (runs) *runs = nrun;
+    P->events_used = 0;
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_launches_per_run(pe_poly *P, uint64_t T, uint32_t *launches)
+{
+    if (!P || !launches) {
+        set_error("NULL argument");
+        return PE_ERR_ARG;
+    }
+    uint32_t n = 0;
+    if (T && P->G) {
+        if (P->E && P->dmax + 1) n++;   // power tables
+        n++;                            // Step A
+        n++;                            // Step B
+    }
+    *launches = n;
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t t0, uint64_t *out,
+                                   void *stream)
+{
+    if (!P) {
+        set_error("NULL poly");
+        return PE_ERR_ARG;
+    }
+    if (T > (1ull << 31)) {
+        set_error("T above 2^31");
+        return PE_ERR_ARG;
+    }
+    BetaArg barg;
+    pe_status st = check_beta(P, beta, &barg);
+    if (st != PE_OK) return st;
+    if (T == 0 || P->G == 0) return PE_OK;
+    if (!out) {
+        set_error("out is NULL");
+        return PE_ERR_ARG;
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    Tiles t;
+    if ((st = plan_for(P, T, &t)) != PE_OK) return st;
+    cudaPointerAttributes attr{};
+    bool dev_out = false;
+    if (cudaPointerGetAttributes(&attr, out) == cudaSuccess)
+        dev_out = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    cudaGetLastError();
+    uint64_t *out_dev = out;
+    cudaError_t e;
+    if (!dev_out) {
+        if ((e = P->out_scratch.ensure(T * P->G * 8)) != cudaSuccess) return cuda_fail(e, "output scratch");
+        out_dev = P->out_scratch.as<uint64_t>();
+    }
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (P->timing) {
+        while (P->events.size() < P->events_used + 4) {
+            cudaEvent_t x;
+            if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(e, "timing events");
+            P->events.push_back(x);
+        }
+        for (int k = 0; k < 4; ++k) ev[k] = P->events[P->events_used + k];
+        P->events_used += 4;
+    }
+    auto mark = [&](int k) {
+        if (ev[k]) cudaEventRecord(ev[k], cs);
+    };
+    const uint32_t dp1 = P->dmax + 1;
+    mark(0);
+    if ((e = launch_powtab(barg, P->E, dp1, P->mc, P->ptab.as<uint64_t>(), cs)) != cudaSuccess)
+        return cuda_fail(e, "power tables");
+    mark(1);
+    if ((e = launch_stepA(P->exps.p, P->exp_bytes, P->s, P->E, P->ptab.as<uint64_t>(), dp1, P->mc,
+                          P->mR.as<uint64_t>(), num_sms(), cs)) != cudaSuccess)
+        return cuda_fail(e, "Step A");
+    const StepBJob J = make_job(P, T, t0, out_dev, false);
+    mark(2);
+    if ((e = launch_stepB((int)t.K, P->variant, J, P->plan.U * P->plan.Q, (int)t.wpb, cs)) != cudaSuccess)
+        return cuda_fail(e, "Step B");
+    mark(3);
+    if (!dev_out) {
+        if ((e = cudaMemcpyAsync(out, out_dev, T * P->G * 8, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+            return cuda_fail(e, "copy back");
+        if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "run");
+    }
+    return PE_OK;
+}

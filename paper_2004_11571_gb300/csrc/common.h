@@ -1,0 +1,50 @@
+// Internal definitions shared by the host library and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pe {
+
+constexpr int kMaxEval = 64;  // evaluated variables x3..xn (n <= 66)
+
+// Per-prime constants, computed once on the host (Sect. 3.1: p is a run-time value).
+struct ModCtx {
+    uint64_t p;         // the modulus, odd, p < 2^62
+    uint64_t p2;        // 2p
+    uint64_t pinv;      // p^-1 mod 2^64
+    uint64_t pinv_neg;  // -p^-1 mod 2^64 (Montgomery reduction)
+    uint64_t r1;        // 2^64 mod p  (Montgomery form of 1)
+    uint64_t r2;        // 2^128 mod p (converts into Montgomery form)
+    uint64_t w64q;      // floor(r1 * 2^64 / p), Barrett quotient for multiplier r1
+    uint64_t one_q;     // floor(2^64 / p), Barrett quotient for multiplier 1
+    double pd;          // (double)p   (Algorithm 2)
+    double ud;          // 1/(double)p rounded to nearest (Algorithm 2)
+};
+
+ModCtx make_modctx(uint64_t p);  // host
+
+struct BetaArg {
+    uint64_t b[kMaxEval];
+};
+
+// Step B arguments for one polynomial (plain kernel) or one job (batched kernel).
+struct StepBJob {
+    const uint64_t *coeffs;   // s, sorted by group
+    const uint64_t *mR;       // s, m_i * 2^64 mod p (Step A output), or nullptr when fused
+    const void *exps;         // E x s exponents (fused Step A)
+    const uint64_t *ptab;     // E x dp1 power tables in Montgomery form (fused Step A)
+    const uint32_t *cs;       // NC+1 chunk starts (term index)
+    const uint32_t *cg;       // NC chunk group ids
+    const int32_t *u_lslot, *u_rslot, *u_lspan, *u_rspan;  // per unit
+    const uint32_t *span_g, *span_base, *span_n;            // per span
+    uint32_t *counters;       // spans x Q arrival counters (self-resetting)
+    ulonglong2 *carry;        // slots x T partial sums (96-bit as lo, hi)
+    ulonglong2 *chain;        // items x Tc chain partials between slabs
+    uint64_t *out;            // T x G
+    uint64_t s, T, t0, G;
+    uint32_t NC, U, Q, kslabs, Tc;
+    uint32_t E, dp1, exp_bytes;
+    ModCtx mc;
+};
+
+}  // namespace pe

@@ -1,0 +1,108 @@
+// Host-side internals shared by the API, batch, tuner and server sources.
+#pragma once
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+#include "../../include/poly_eval.h"
+#include "common.h"
+
+namespace pe {
+
+void set_error(const char *fmt, ...);
+pe_status cuda_fail(cudaError_t e, const char *what);
+
+// Owned device allocation that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t n)
+    {
+        if (n <= bytes && p) return cudaSuccess;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n;
+        return cudaSuccess;
+    }
+    template <typename T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Work decomposition of Step B for one (polynomial, tile shape, T).
+struct Plan {
+    bool valid = false;
+    uint32_t K = 0, kslabs = 0, Q = 0, Tc = 0, wpb = 0;
+    uint64_t T = 0;
+    uint32_t NC = 0, U = 0, S = 0, nslots = 0;
+    DevBuf cs, cg, unit, span, counters, carry, chain;
+    uint64_t scratch_bytes() const { return counters.bytes + carry.bytes + chain.bytes; }
+};
+
+struct HostChunks {
+    uint32_t K = 0;
+    std::vector<uint32_t> cs, cg;       // NC+1, NC
+    std::vector<uint32_t> gfirst;       // first chunk of each group, G+1
+};
+
+struct Tiles {
+    uint32_t K = 0, kslabs = 0, Tc = 0, wpb = 0;
+};
+
+}  // namespace pe
+
+struct pe_poly {
+    uint64_t p = 0;
+    uint32_t n = 0, E = 0;
+    uint64_t s = 0, G = 0;
+    int variant = 0;             // resolved pe_variant
+    pe::ModCtx mc{};
+    uint32_t exp_bytes = 1;      // 1 or 2 on the device
+    uint32_t dmax = 0;           // max exponent over x3..xn
+    std::vector<uint64_t> group_off;   // G+1 (host)
+    std::vector<uint32_t> keys;        // 2G (host)
+    pe::DevBuf coeffs, exps, mR, ptab, out_scratch;
+    pe::HostChunks chunks;
+    pe::Plan plan;
+    pe_tiles forced{};
+    bool timing = false;
+    std::vector<cudaEvent_t> events;   // 4 per timed run
+    size_t events_used = 0;
+    ~pe_poly()
+    {
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+    }
+    uint64_t device_bytes() const
+    {
+        return coeffs.bytes + exps.bytes + mR.bytes + ptab.bytes + out_scratch.bytes + plan.cs.bytes +
+               plan.cg.bytes + plan.unit.bytes + plan.span.bytes + plan.scratch_bytes();
+    }
+};
+
+namespace pe {
+int num_sms();
+// Chooses the tile shape for a run of T points (forced fields win).
+Tiles choose_tiles(pe_poly *poly, uint64_t T, const pe_tiles *forced);
+// Builds (or reuses) the plan for the given tiles and T.
+pe_status ensure_plan(pe_poly *poly, const Tiles &t, uint64_t T);
+// Fills a Step B job description from a poly and its current plan.
+StepBJob make_job(pe_poly *poly, uint64_t T, uint64_t t0, uint64_t *out_dev, bool fused);
+pe_status check_beta(const pe_poly *poly, const uint64_t *beta, BetaArg *arg);
+// Cost model of one tile shape (relative time units), used by choose_tiles and the batch planner.
+double estimate_cost(uint64_t NC, uint32_t K, uint32_t kslabs, uint64_t Tc, uint64_t T, uint64_t R);
+}  // namespace pe

@@ -1,0 +1,15 @@
+// Host-side launchers of the library's kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include "common.h"
+
+namespace pe {
+
+cudaError_t launch_powtab(const BetaArg &beta, uint32_t E, uint32_t dp1, const ModCtx &mc, uint64_t *ptab,
+                          cudaStream_t st);
+cudaError_t launch_stepA(const void *exps, uint32_t exp_bytes, uint64_t s, uint32_t E, const uint64_t *ptab,
+                         uint32_t dp1, const ModCtx &mc, uint64_t *mR, int num_sms, cudaStream_t st);
+cudaError_t launch_stepB(int K, int var, const StepBJob &J, uint32_t nitems, int wpb, cudaStream_t st);
+cudaError_t stepB_occupancy(int K, int var, int wpb, int *blocks_per_sm);
+
+}  // namespace pe

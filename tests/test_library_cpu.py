@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads and exports every declared entry point;
+host-side validation rejects bad inputs before any device work (no GPU)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_2004_11571_gb300 as pe
+from paper_2004_11571_gb300 import _build
+
+
+@pytest.fixture(scope="module")
+def L():
+    _build.build()
+    return pe.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = pe.declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def _create(L, p, coeffs, exps, variant=0):
+    coeffs = np.ascontiguousarray(coeffs, np.uint64)
+    exps = np.ascontiguousarray(exps, np.uint32)
+    d = pe._Desc(p, exps.shape[1], 4, coeffs.shape[0], coeffs.ctypes.data, exps.ctypes.data, 0, variant)
+    h = ctypes.c_void_p()
+    return L.poly_eval_create(ctypes.byref(d), ctypes.byref(h)), h
+
+
+def test_validation_before_device_work(L):
+    p = (1 << 61) - 1
+    ok_c = [1, 2, 3]
+    ok_e = [[1, 0, 2], [0, 1, 3], [0, 0, 1]]
+    assert _create(L, p + 1, ok_c, ok_e)[0] == 2                    # even p
+    assert _create(L, 1, ok_c, ok_e)[0] == 2                        # p < 3
+    assert _create(L, (1 << 62) + 1, ok_c, ok_e)[0] == 2            # above 2^62
+    assert _create(L, p, ok_c, ok_e, variant=2)[0] == 2             # FP64 needs p < 2^50
+    assert _create(L, p, [1, p, 3], ok_e)[0] == 3                   # coefficient not reduced
+    assert _create(L, p, ok_c, [[1, 0, 2], [0, 1, 70000], [0, 0, 1]])[0] == 4   # exponent range
+    assert _create(L, p, ok_c, ok_e, variant=9)[0] == 1             # unknown variant
+    d = pe._Desc(p, 1, 4, 0, None, None, 0, 0)
+    h = ctypes.c_void_p()
+    assert L.poly_eval_create(ctypes.byref(d), ctypes.byref(h)) == 1  # n < 2
+    assert L.poly_eval_create(None, ctypes.byref(h)) == 1
+    assert b"n = 1" in L.poly_eval_last_error() or L.poly_eval_last_error()
+
+
+def test_binding_raises_without_library(monkeypatch):
+    monkeypatch.setattr(pe, "_lib", None)
+    monkeypatch.setattr(pe, "LIB_PATH", "/nonexistent/libpolyeval.so")
+    with pytest.raises(RuntimeError):
+        pe.lib()

@@ -1,0 +1,182 @@
+"""Bit-exact parity of the CUDA path with the oracle (GPU).
+
+Tolerance is zero: the images are elements of F_p and the modular result is
+unique, so every variant and every tile shape must agree exactly with the
+oracle.  Medium cases are compared cell for cell; the full-size workloads
+are compared on seeded samples of cells, with the properties that hold at
+any size (canonical range, agreement between variants) checked everywhere.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2004_11571_gb300 as pe  # noqa: E402
+
+P62 = wl.random_prime(62, 21)
+P50 = wl.random_prime(50, 22)
+
+
+def _gpu(w, variant="auto", tiles=None, T=None, t0=None):
+    poly = pe.Poly.from_workload(w, variant=variant)
+    if tiles:
+        poly.set_tiles(**tiles)
+    out = poly.run(w.beta, w.T if T is None else T, w.t0 if t0 is None else t0)
+    torch.cuda.synchronize()
+    keys = poly.groups()
+    got = pe.to_u64(out)
+    poly.close()
+    return keys, got
+
+
+def _check_full(w, variant="auto", tiles=None, t0=None):
+    keys_ref, ref = oracle.eval_direct(w, t0=t0)
+    keys, got = _gpu(w, variant, tiles, t0=t0)
+    assert np.array_equal(keys, keys_ref)
+    assert got.shape == ref.shape
+    bad = np.argwhere(got != ref)
+    assert bad.size == 0, f"{len(bad)} cells differ, first {bad[:3].tolist()}"
+
+
+def test_tiny_config_all_variants():
+    w = wl.config_tiny()
+    for v in ("barrett64", "mont64", "auto"):
+        _check_full(w, v)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("variant", ["barrett64", "mont64"])
+def test_tile_shapes_zipf(K, variant):
+    # Zipf groups: sizes from thousands of terms down to 1, so items cut groups
+    # at every kind of boundary.
+    w = wl.make_zipf(n=7, s=30_000, p=P62, deg12=20, deg_rest=9, T=77, seed=5, a=1.1)
+    for slabs, tchunk in [(1, 32), (2, 50), (3, 77), (5, 40)]:
+        _check_full(w, variant, dict(K=K, slabs=slabs, tchunk=tchunk, warps_per_block=2))
+
+
+@pytest.mark.parametrize("K", [1, 4, 8])
+def test_fp64_variant(K):
+    w = wl.make_zipf(n=6, s=20_000, p=P50, deg12=12, deg_rest=6, T=70, seed=6)
+    _check_full(w, "fp64", dict(K=K, slabs=2, tchunk=45))
+    _check_full(w, "fp64")
+    _check_full(w, "barrett64")
+
+
+def test_automatic_tiles_and_ragged_sizes():
+    for seed, (n, s, d12, dr, T) in enumerate([(6, 12_345, 8, 5, 100), (9, 40_001, 30, 20, 129),
+                                                (12, 3_333, 3, 10, 1), (3, 50_000, 2, 50, 33)]):
+        w = wl.make_uniform(n=n, s=s, p=P62, deg12=d12, deg_rest=dr, T=T, seed=seed)
+        _check_full(w)
+
+
+@pytest.mark.parametrize("t0", [0, 1, 7, 123_456, 1 << 40])
+def test_start_points(t0):
+    w = wl.make_uniform(n=5, s=5_000, p=P62, deg12=6, deg_rest=7, T=70, seed=9)
+    _check_full(w, "barrett64", dict(K=4, slabs=1, tchunk=32), t0=t0)
+    _check_full(w, "mont64", None, t0=t0)
+
+
+def test_t0_zero_and_beta_one_are_coefficient_sums():
+    w = wl.make_uniform(n=8, s=9_000, p=P62, deg12=9, deg_rest=9, T=40, seed=10)
+    _, got = _gpu(w, t0=0)
+    keys, tg = oracle.group_keys(w.exps)
+    sums = np.zeros(keys.shape[0], dtype=object)
+    for c, g in zip(w.coeffs.tolist(), tg.tolist()):
+        sums[g] = (sums[g] + c) % w.p
+    assert got[0].tolist() == sums.tolist()
+    w1 = wl.Workload(p=w.p, n=w.n, coeffs=w.coeffs, exps=w.exps, beta=np.ones(w.n - 2, np.uint64), T=5)
+    _, got1 = _gpu(w1)
+    for r in range(5):
+        assert got1[r].tolist() == sums.tolist()
+
+
+def test_degenerate_shapes():
+    # n = 2 (nothing evaluated), one group, one term per group, empty input.
+    w2 = wl.make_uniform(n=2, s=3_000, p=P62, deg12=40, deg_rest=0, T=9, seed=11)
+    _check_full(w2)
+    w1g = wl.make_uniform(n=6, s=20_000, p=P62, deg12=0, deg_rest=8, T=65, seed=12)
+    _check_full(w1g)
+    _check_full(w1g, "barrett64", dict(K=16, slabs=4, tchunk=64))
+    wsing = wl.make_uniform(n=6, s=500, p=P62, deg12=1000, deg_rest=4, T=33, seed=13)
+    _check_full(wsing)
+    wone = wl.make_uniform(n=6, s=1, p=P62, deg12=3, deg_rest=4, T=3, seed=14)
+    _check_full(wone)
+    empty = wl.Workload(p=P62, n=4, coeffs=np.zeros(0, np.uint64), exps=np.zeros((0, 4), np.uint32),
+                        beta=np.array([2, 3], np.uint64), T=4)
+    poly = pe.Poly.from_workload(empty)
+    assert poly.G == 0
+    poly.run(empty.beta, 4)
+    poly.close()
+
+
+def test_unsorted_input_and_u16_exponents():
+    w = wl.make_uniform(n=5, s=8_000, p=P62, deg12=7, deg_rest=300, T=40, seed=15, sort=False)
+    assert w.exps.dtype == np.uint16
+    _check_full(w)
+    _check_full(wl.shuffled(wl.make_zipf(n=6, s=10_000, p=P62, deg12=10, deg_rest=5, T=35, seed=16), 3))
+
+
+def test_small_prime_and_host_output():
+    w = wl.make_uniform(n=6, s=4_000, p=101, deg12=5, deg_rest=5, T=50, seed=17)
+    _check_full(w)
+    keys_ref, ref = oracle.eval_direct(w)
+    poly = pe.Poly.from_workload(w)
+    host = np.zeros((w.T, poly.G), np.uint64)
+    poly.run(w.beta, w.T, w.t0, out=host)
+    assert np.array_equal(host, ref)
+    poly.close()
+
+
+def test_errors_are_reported():
+    w = wl.config_tiny()
+    poly = pe.Poly.from_workload(w)
+    bad = w.beta.copy()
+    bad[1] = 0
+    with pytest.raises(pe.PolyEvalError) as e:
+        poly.run(bad, 4)
+    assert e.value.status == 1
+    bad[1] = w.p
+    with pytest.raises(pe.PolyEvalError):
+        poly.run(bad, 4)
+    with pytest.raises(pe.PolyEvalError) as e:
+        pe.Poly.from_workload(w, variant="fp64")           # 62-bit prime on the FP64 path
+    assert e.value.status == 2
+    poly.close()
+
+
+def _sample_cells(w, G, n, seed):
+    rnd = np.random.default_rng(seed)
+    rows = np.concatenate([[0, w.T - 1], rnd.integers(0, w.T, n - 2)])
+    cols = np.concatenate([[0, G - 1], rnd.integers(0, G, n - 2)])
+    return rows, cols
+
+
+@pytest.mark.parametrize("name", ["large", "width62", "width50"])
+def test_full_size_configs_sampled(name):
+    if name == "large":
+        w = wl.config_large()
+        variants = ["auto", "mont64"]
+    elif name == "width62":
+        w = wl.config_width(62)
+        variants = ["auto", "mont64"]
+    else:
+        w = wl.config_width(50)
+        variants = ["fp64", "auto"]
+    cells = oracle.CellOracle(w)
+    outs = []
+    for v in variants:
+        keys, got = _gpu(w, v)
+        assert np.array_equal(keys, cells.keys)
+        assert int(got.max()) < w.p
+        outs.append(got)
+    assert np.array_equal(outs[0], outs[1])            # variants agree everywhere
+    rows, cols = _sample_cells(w, cells.G, 48, 1)
+    want = cells(rows + w.t0, cols)
+    assert np.array_equal(outs[0][rows, cols], want)
