@@ -67,11 +67,12 @@ template <int K, int VAR>
 static cudaError_t launch_b(const StepBJob &J, uint32_t nitems, int wpb, cudaStream_t st, int *occ)
 {
     const size_t smem = (size_t)wpb * sizeof(WarpSmem);
-    static bool attr_set[9] = {false};
-    if (!attr_set[wpb]) {
-        cudaError_t e = cudaFuncSetAttribute(k_stepB<K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static bool attr_set = false;   // once, at the largest block (8 warps)
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_stepB<K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(8 * sizeof(WarpSmem)));
         if (e != cudaSuccess) return e;
-        attr_set[wpb] = true;
+        attr_set = true;
     }
     if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_stepB<K, VAR>, wpb * 32, smem);
     if (nitems == 0) return cudaSuccess;
