@@ -185,6 +185,30 @@ pe_status poly_eval_kernel_times(pe_poly *poly, double ms[3], uint64_t *runs);
 /* Number of kernel launches one poly_eval_run issues (for launch accounting). */
 pe_status poly_eval_launches_per_run(pe_poly *poly, uint64_t T, uint32_t *launches);
 
+/*
+ * Step B for callers that cannot allocate device memory.  The paper has no
+ * counterpart; it exists because some callers may not call cudaMalloc (code
+ * inside another framework's memory pool, embedded runtimes without allocator
+ * access, processes that must not grow after start-up).  It allocates
+ * nothing: all scratch comes from one fixed 32 MiB device array that the
+ * library reserves on every GPU where it is loaded, until the process exits.
+ *   p         : odd, 3 <= p < 2^62 (Barrett product).
+ *   coeffs    : device, s coefficients a_i < p, sorted so that each group's
+ *               terms are contiguous, groups in output-column order.
+ *   m         : device, s monomial values m_i = M_i(beta) in [0, p) (Step A).
+ *   group_off : device, G+1 uint32 offsets: group g is terms
+ *               group_off[g] .. group_off[g+1]-1 (nonempty, group_off[G] = s).
+ *   out       : device, T x G, row r = image at point t0 + r.
+ * Asynchronous on `stream`.  The first call on a device looks up the scratch
+ * address with that device current; make it before any stream capture.
+ * Every call shares the one array, so calls that overlap on the GPU race:
+ * serialise them (one stream, or events).  Inputs whose s*T needs more than
+ * the fixed scratch are rejected with PE_ERR_ARG and a message.
+ */
+pe_status poly_eval_stepb_noalloc(uint64_t p, uint64_t s, uint64_t G, const uint64_t *coeffs,
+                                  const uint64_t *m, const uint32_t *group_off, uint64_t T, uint64_t t0,
+                                  uint64_t *out, void *stream);
+
 /* -------------------------------------------------------------------------
  * Batched evaluation: many polynomials, each with its own beta, T, t0 and
  * prime, evaluated by one persistent kernel with a device-side work queue.

@@ -274,6 +274,19 @@ class Poly:
             pass
 
 
+def stepb_noalloc(p: int, coeffs, m, group_off, T: int, t0: int, out, stream=None):
+    """poly_eval_stepb_noalloc on CUDA tensors: coeffs, m (int64 views of
+    uint64), group_off (int32 view of uint32, G+1 entries) and out (T x G)."""
+    L = lib()
+    fn = L.poly_eval_stepb_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [_u64, _u64, _u64, _vp, _vp, _vp, _u64, _u64, _vp, _vp]
+    s, G = int(coeffs.shape[0]), int(group_off.shape[0]) - 1
+    _check(fn(int(p), s, G, coeffs.data_ptr(), m.data_ptr(), group_off.data_ptr(), int(T), int(t0),
+              out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
 def modmul_peak(variant="barrett64", p: int = (1 << 61) - 1):
     """(term-points/s, SM MHz) of the register-only Step B inner loop."""
     tps, mhz = ctypes.c_double(), ctypes.c_double()
