@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="large", choices=["large", "tiny", "width62", "width50"])
+    ap.add_argument("--config", default="large", choices=["large", "tiny", "width62", "width50", "batched"])
+    ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -283,10 +284,77 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """Config of 512 independent polynomials: one CUDA-graph launch of the
+    persistent kernel vs a loop of per-polynomial poly_eval_run calls."""
+    import torch
+    import paper_2004_11571_gb300 as pe
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    t_gen = time.perf_counter()
+    ws = wl.config_batched(count=args.batch_count)
+    t_gen = time.perf_counter() - t_gen
+    t_create = time.perf_counter()
+    polys = [pe.Poly.from_workload(w) for w in ws]
+    t_create = time.perf_counter() - t_create
+    outs = [torch.empty((w.T, p.G), dtype=torch.int64, device="cuda") for w, p in zip(ws, polys)]
+    t0s = [1 + rank * w.T for w in ws]
+    tp = sum(w.s * w.T for w in ws)
+    t_plan = time.perf_counter()
+    batch = pe.Batch([(p, w.beta, w.T, t0, o) for p, w, t0, o in zip(polys, ws, t0s, outs)])
+    t_plan = time.perf_counter() - t_plan
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for a, b2 in evs:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b2.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b2) for a, b2 in evs]
+
+    def loop():
+        for p, w, t0, o in zip(polys, ws, t0s, outs):
+            p.run(w.beta, w.T, t0, out=o, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        batch.launch(stream)
+        loop()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_batch = timed(lambda: batch.launch(stream), args.steps)
+    ms_loop = timed(loop, max(1, args.steps // 2))
+    clk = clocks.stop()
+    v_batch = tp / (statistics.mean(ms_batch) * 1e-3)
+    v_loop = tp / (statistics.mean(ms_loop) * 1e-3)
+    if rank != 0:
+        return
+    line = {"metric": "term-point evaluations/s (batched)", "value": v_batch * world, "unit": "term-points/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms_batch),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"batched {len(ws)} polynomials, n 6..12, s log-uniform 1e3..1e6, "
+                                   "D 5..60, T in {64,256,1024,2048}, 50/62-bit primes",
+                       "term_points": tp, "terms": sum(w.s for w in ws), "jobs": len(ws),
+                       "l2": "flushed between timed steps by a 256 MB device write"},
+            "clocks": clk, "plain_loop": {"value": v_loop, "ms_per_step": statistics.mean(ms_loop),
+                                          "launches": sum(p.launches_per_run(w.T) for p, w in zip(polys, ws))},
+            "batched_over_plain_loop": v_batch / v_loop, "gpu_launches": 2 * args.steps,
+            "host_seconds": {"generate": t_gen, "create": t_create, "plan_and_capture": t_plan}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

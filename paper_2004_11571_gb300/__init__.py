@@ -274,6 +274,63 @@ class Poly:
             pass
 
 
+class Batch:
+    """A planned batch (poly_eval_batch_plan): one CUDA graph running every job's
+    power tables and a persistent Step A+B kernel over a shared work queue.
+
+    jobs: sequence of (poly, beta, T, t0, out) with `out` a CUDA tensor (T x G)."""
+
+    def __init__(self, jobs):
+        L = lib()
+        n = len(jobs)
+        arr = (_Job * max(n, 1))()
+        self._keep = []
+        for i, (poly, beta, T, t0, out) in enumerate(jobs):
+            b = np.ascontiguousarray(np.asarray(beta, dtype=np.uint64).reshape(-1))
+            self._keep.append(b)
+            arr[i] = _Job(poly.handle.value, b.ctypes.data if b.size else None, int(T), int(t0), out.data_ptr())
+        self._keep.append(arr)
+        self.polys = [j[0] for j in jobs]
+        h = ctypes.c_void_p()
+        _check(L.poly_eval_batch_plan(arr, n, ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().poly_eval_batch_launch(self._h, _stream_ptr(stream)))
+
+    def set_beta(self, j: int, beta):
+        b = np.ascontiguousarray(np.asarray(beta, dtype=np.uint64).reshape(-1))
+        _check(lib().poly_eval_batch_set_beta(self._h, int(j), b.ctypes.data if b.size else None))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().poly_eval_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tune(poly: "Poly", T: int):
+    """Autotunes the tile shape and modular product for poly's shape bucket;
+    returns (tiles dict, milliseconds per run)."""
+    t = _Tiles()
+    ms = ctypes.c_double()
+    _check(lib().poly_eval_tune(poly.handle, int(T), ctypes.byref(t), ctypes.byref(ms)))
+    return {"K": t.K, "slabs": t.slabs, "tchunk": t.tchunk, "warps_per_block": t.warps_per_block}, ms.value
+
+
+def tune_save(path: str):
+    _check(lib().poly_eval_tune_save(path.encode()))
+
+
+def tune_load(path: str):
+    _check(lib().poly_eval_tune_load(path.encode()))
+
+
 def stepb_noalloc(p: int, coeffs, m, group_off, T: int, t0: int, out, stream=None):
     """poly_eval_stepb_noalloc on CUDA tensors: coeffs, m (int64 views of
     uint64), group_off (int32 view of uint32, G+1 entries) and out (T x G)."""

@@ -7,6 +7,7 @@
 #include <numeric>
 #include "internal.h"
 #include "kernels.h"
+#include "tune.h"
 
 namespace pe {
 
@@ -101,9 +102,12 @@ double estimate_cost(uint64_t NC, uint32_t K, uint32_t kslabs, uint64_t Tc, uint
 Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
 {
     Tiles t;
-    t.wpb = (f && f->warps_per_block) ? f->warps_per_block : 4;
+    const TuneEntry *te = tune_lookup(P, T);
+    t.wpb = (f && f->warps_per_block) ? f->warps_per_block : (te ? te->wpb : 4);
     if (f && f->K) {
         t.K = f->K;
+    } else if (te) {
+        t.K = te->K;
     } else {
         // Padded slots plus the per-chunk walk: a chunk costs K products+sums
         // and one walk entry (~0.7 of a product+sum) per point.
@@ -149,7 +153,7 @@ Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
     return t;
 }
 
-static void build_chunks(pe_poly *P, uint32_t K)
+void build_chunks(pe_poly *P, uint32_t K)
 {
     HostChunks &h = P->chunks;
     if (h.K == K && !h.cs.empty()) return;
@@ -168,19 +172,20 @@ static void build_chunks(pe_poly *P, uint32_t K)
     h.cs.push_back((uint32_t)P->s);
 }
 
-pe_status ensure_plan(pe_poly *P, const Tiles &t, uint64_t T)
+void build_plan_host(pe_poly *P, const Tiles &t, uint64_t T, PlanHost &ph)
 {
-    Plan &pl = P->plan;
-    if (pl.valid && pl.K == t.K && pl.kslabs == t.kslabs && pl.Tc == t.Tc && pl.T == T && pl.wpb == t.wpb)
-        return PE_OK;
-    pl.valid = false;
     build_chunks(P, t.K);
     const HostChunks &h = P->chunks;
-    const uint32_t NC = (uint32_t)h.cg.size();
+    ph.K = t.K;
+    ph.kslabs = t.kslabs;
+    ph.Tc = t.Tc;
+    ph.wpb = t.wpb;
+    ph.T = T;
+    ph.NC = (uint32_t)h.cg.size();
     const uint32_t per_unit = 32u * t.kslabs;
-    const uint32_t U = (NC + per_unit - 1) / per_unit;
-    const uint32_t Q = (uint32_t)((T + t.Tc - 1) / t.Tc);
-    std::vector<int32_t> unit(4 * (size_t)U, -1);   // lslot, rslot, lspan, rspan
+    ph.U = (ph.NC + per_unit - 1) / per_unit;
+    ph.Q = (uint32_t)((T + t.Tc - 1) / t.Tc);
+    ph.unit.assign(4 * (size_t)ph.U, -1);   // lslot, rslot, lspan, rspan
     std::vector<uint32_t> sg, sbase, sn;
     uint32_t nslots = 0;
     for (uint64_t g = 0; g < P->G; ++g) {
@@ -190,34 +195,89 @@ pe_status ensure_plan(pe_poly *P, const Tiles &t, uint64_t T)
         sg.push_back((uint32_t)g);
         sbase.push_back(nslots);
         sn.push_back(ub - ua + 1);
-        unit[1 * (size_t)U + ua] = (int32_t)nslots;
-        unit[3 * (size_t)U + ua] = sp;
+        ph.unit[1 * (size_t)ph.U + ua] = (int32_t)nslots;
+        ph.unit[3 * (size_t)ph.U + ua] = sp;
         for (uint32_t u = ua + 1; u <= ub; ++u) {
-            unit[0 * (size_t)U + u] = (int32_t)(nslots + (u - ua));
-            unit[2 * (size_t)U + u] = sp;
+            ph.unit[0 * (size_t)ph.U + u] = (int32_t)(nslots + (u - ua));
+            ph.unit[2 * (size_t)ph.U + u] = sp;
         }
         nslots += ub - ua + 1;
     }
-    const uint32_t S = (uint32_t)sg.size();
-    std::vector<uint32_t> span(3 * (size_t)std::max<uint32_t>(S, 1));
-    for (uint32_t i = 0; i < S; ++i) {
-        span[i] = sg[i];
-        span[S + i] = sbase[i];
-        span[2 * (size_t)S + i] = sn[i];
+    ph.S = (uint32_t)sg.size();
+    ph.nslots = nslots;
+    ph.span.assign(3 * (size_t)std::max<uint32_t>(ph.S, 1), 0);
+    for (uint32_t i = 0; i < ph.S; ++i) {
+        ph.span[i] = sg[i];
+        ph.span[ph.S + i] = sbase[i];
+        ph.span[2 * (size_t)ph.S + i] = sn[i];
     }
+}
+
+size_t PlanHost::counter_bytes() const { return (size_t)std::max<uint32_t>(S, 1) * Q * 4; }
+size_t PlanHost::carry_bytes() const { return nslots ? (size_t)nslots * T * 16 : 16; }
+size_t PlanHost::chain_bytes() const { return kslabs > 1 ? (size_t)U * Q * Tc * 16 : 16; }
+
+void fill_job(StepBJob &J, pe_poly *P, const PlanHost &ph, const uint32_t *cs, const uint32_t *cg,
+              const int32_t *unit, const uint32_t *span, uint32_t *counters, ulonglong2 *carry, ulonglong2 *chain,
+              uint64_t t0, uint64_t *out_dev, const uint64_t *mR, const uint64_t *ptab, int variant)
+{
+    J = StepBJob{};
+    J.coeffs = P->coeffs.as<uint64_t>();
+    J.mR = mR;
+    J.exps = P->exps.p;
+    J.ptab = ptab;
+    J.cs = cs;
+    J.cg = cg;
+    J.u_lslot = unit;
+    J.u_rslot = unit + ph.U;
+    J.u_lspan = unit + 2 * (size_t)ph.U;
+    J.u_rspan = unit + 3 * (size_t)ph.U;
+    const uint32_t S = std::max<uint32_t>(ph.S, 1);
+    J.span_g = span;
+    J.span_base = span + S;
+    J.span_n = span + 2 * (size_t)S;
+    J.counters = counters;
+    J.carry = carry;
+    J.chain = chain;
+    J.out = out_dev;
+    J.s = P->s;
+    J.T = ph.T;
+    J.t0 = t0;
+    J.G = P->G;
+    J.NC = ph.NC;
+    J.U = ph.U;
+    J.Q = ph.Q;
+    J.kslabs = ph.kslabs;
+    J.Tc = ph.Tc;
+    J.E = P->E;
+    J.dp1 = P->dmax + 1;
+    J.exp_bytes = P->exp_bytes;
+    J.K = ph.K;
+    J.var = (uint32_t)variant;
+    J.mc = P->mc;
+}
+
+pe_status ensure_plan(pe_poly *P, const Tiles &t, uint64_t T)
+{
+    Plan &pl = P->plan;
+    if (pl.valid && pl.K == t.K && pl.kslabs == t.kslabs && pl.Tc == t.Tc && pl.T == T && pl.wpb == t.wpb)
+        return PE_OK;
+    pl.valid = false;
+    PlanHost &ph = pl.host;
+    build_plan_host(P, t, T, ph);
+    const HostChunks &h = P->chunks;
     cudaError_t e;
     if ((e = pl.cs.ensure(h.cs.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
     if ((e = pl.cg.ensure(std::max<size_t>(h.cg.size(), 1) * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
-    if ((e = pl.unit.ensure(unit.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
-    if ((e = pl.span.ensure(span.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
-    if ((e = pl.counters.ensure((size_t)std::max<uint32_t>(S, 1) * Q * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
-    if ((e = pl.carry.ensure(nslots ? (size_t)nslots * T * 16 : 16)) != cudaSuccess) return cuda_fail(e, "carry alloc");
-    const size_t chain_bytes = t.kslabs > 1 ? (size_t)U * Q * t.Tc * 16 : 16;
-    if ((e = pl.chain.ensure(chain_bytes)) != cudaSuccess) return cuda_fail(e, "chain alloc");
+    if ((e = pl.unit.ensure(ph.unit.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
+    if ((e = pl.span.ensure(ph.span.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
+    if ((e = pl.counters.ensure(ph.counter_bytes())) != cudaSuccess) return cuda_fail(e, "plan alloc");
+    if ((e = pl.carry.ensure(ph.carry_bytes())) != cudaSuccess) return cuda_fail(e, "carry alloc");
+    if ((e = pl.chain.ensure(ph.chain_bytes())) != cudaSuccess) return cuda_fail(e, "chain alloc");
     if ((e = cudaMemcpy(pl.cs.p, h.cs.data(), h.cs.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (NC && (e = cudaMemcpy(pl.cg.p, h.cg.data(), h.cg.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) ||
-        (e = cudaMemcpy(pl.unit.p, unit.data(), unit.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(pl.span.p, span.data(), span.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ph.NC && (e = cudaMemcpy(pl.cg.p, h.cg.data(), h.cg.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(pl.unit.p, ph.unit.data(), ph.unit.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(pl.span.p, ph.span.data(), ph.span.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(pl.counters.p, 0, pl.counters.bytes)) != cudaSuccess)
         return cuda_fail(e, "plan upload");
     pl.K = t.K;
@@ -225,11 +285,11 @@ pe_status ensure_plan(pe_poly *P, const Tiles &t, uint64_t T)
     pl.Tc = t.Tc;
     pl.wpb = t.wpb;
     pl.T = T;
-    pl.NC = NC;
-    pl.U = U;
-    pl.Q = Q;
-    pl.S = S;
-    pl.nslots = nslots;
+    pl.NC = ph.NC;
+    pl.U = ph.U;
+    pl.Q = ph.Q;
+    pl.S = ph.S;
+    pl.nslots = ph.nslots;
     pl.valid = true;
     return PE_OK;
 }
@@ -237,39 +297,12 @@ pe_status ensure_plan(pe_poly *P, const Tiles &t, uint64_t T)
 StepBJob make_job(pe_poly *P, uint64_t T, uint64_t t0, uint64_t *out_dev, bool fused)
 {
     const Plan &pl = P->plan;
-    StepBJob J{};
-    J.coeffs = P->coeffs.as<uint64_t>();
-    J.mR = fused ? nullptr : P->mR.as<uint64_t>();
-    J.exps = P->exps.p;
-    J.ptab = P->ptab.as<uint64_t>();
-    J.cs = pl.cs.as<uint32_t>();
-    J.cg = pl.cg.as<uint32_t>();
-    const int32_t *unit = pl.unit.as<int32_t>();
-    J.u_lslot = unit;
-    J.u_rslot = unit + pl.U;
-    J.u_lspan = unit + 2 * (size_t)pl.U;
-    J.u_rspan = unit + 3 * (size_t)pl.U;
-    const uint32_t S = std::max<uint32_t>(pl.S, 1);
-    J.span_g = pl.span.as<uint32_t>();
-    J.span_base = J.span_g + S;
-    J.span_n = J.span_g + 2 * (size_t)S;
-    J.counters = pl.counters.as<uint32_t>();
-    J.carry = pl.carry.as<ulonglong2>();
-    J.chain = pl.chain.as<ulonglong2>();
-    J.out = out_dev;
-    J.s = P->s;
-    J.T = T;
-    J.t0 = t0;
-    J.G = P->G;
-    J.NC = pl.NC;
-    J.U = pl.U;
-    J.Q = pl.Q;
-    J.kslabs = pl.kslabs;
-    J.Tc = pl.Tc;
-    J.E = P->E;
-    J.dp1 = P->dmax + 1;
-    J.exp_bytes = P->exp_bytes;
-    J.mc = P->mc;
+    StepBJob J;
+    fill_job(J, P, pl.host, pl.cs.as<uint32_t>(), pl.cg.as<uint32_t>(), pl.unit.as<int32_t>(),
+             pl.span.as<uint32_t>(), pl.counters.as<uint32_t>(), pl.carry.as<ulonglong2>(),
+             pl.chain.as<ulonglong2>(), t0, out_dev, fused ? nullptr : P->mR.as<uint64_t>(),
+             P->ptab.as<uint64_t>(), P->variant);
+    (void)T;
     return J;
 }
 
@@ -333,8 +366,8 @@ extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
         return PE_ERR_ARG;
     }
     int variant = d->variant;
-    if (variant == PE_MODMUL_AUTO) variant = PE_MODMUL_BARRETT64;
-    if (variant != PE_MODMUL_MONT64 && variant != PE_MODMUL_FP64 && variant != PE_MODMUL_BARRETT64) {
+    if (variant != PE_MODMUL_AUTO && variant != PE_MODMUL_MONT64 && variant != PE_MODMUL_FP64 &&
+        variant != PE_MODMUL_BARRETT64) {
         set_error("unknown variant %d", (int)d->variant);
         return PE_ERR_ARG;
     }
@@ -392,7 +425,8 @@ extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
     P->n = n;
     P->E = E;
     P->s = s;
-    P->variant = variant;
+    P->requested_variant = variant;
+    P->variant = variant == PE_MODMUL_AUTO ? PE_MODMUL_BARRETT64 : variant;
     P->mc = make_modctx(d->p);
     P->dmax = dmax;
     P->exp_bytes = dmax <= 0xff ? 1 : 2;
@@ -472,6 +506,11 @@ extern "C" pe_status poly_eval_set_tiles(pe_poly *P, const pe_tiles *t)
 
 static pe_status plan_for(pe_poly *P, uint64_t T, Tiles *tiles)
 {
+    const int v = run_variant(P, T);
+    if (v != P->variant) {
+        P->variant = v;
+        P->plan.valid = false;
+    }
     *tiles = choose_tiles(P, T, &P->forced);
     return ensure_plan(P, *tiles, T);
 }

@@ -1,0 +1,404 @@
+// Batched evaluation: many polynomials in one persistent kernel.
+//
+// Each job (polynomial, beta, T, t0) gets its own Step B plan; all plans,
+// power tables and scratch live in one device arena.  Work items of every job
+// are put in one queue ordered by decreasing estimated cost; a persistent
+// kernel with a fixed number of warps per SM pops items with an atomic ticket
+// (a warp that finishes early takes the next item, so the cheap items at the
+// end of the queue fill the tail).  Step A runs fused into each item (the
+// monomial values are formed from the exponents and the job's power tables),
+// so a batch is three graph nodes: clear the counters, build every job's power
+// tables, run the queue.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include "internal.h"
+#include "modarith.cuh"
+#include "stepb.cuh"
+#include "tune.h"
+
+namespace pe {
+
+struct PowJob {
+    const uint64_t *beta;
+    uint64_t *ptab;
+    uint32_t E, dp1;
+    ModCtx mc;
+};
+
+// Power tables of every job: blockIdx.y selects the job (Sect. 2.3 tables).
+__global__ void k_powtab_batch(const PowJob *__restrict__ jobs)
+{
+    const PowJob &J = jobs[blockIdx.y];
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= J.E * J.dp1) return;
+    const uint32_t j = idx / J.dp1, e = idx - j * J.dp1;
+    const uint64_t bR = canon(mont_mul(J.beta[j], J.mc.r2, J.mc), J.mc.p);
+    J.ptab[idx] = mont_pow(bR, e, J.mc);
+}
+
+struct QueueSmem {
+    WarpSmem w;
+    StepBJob job;
+};
+
+template <int K, int VAR>
+__device__ __forceinline__ void queue_item(const StepBJob &J, uint32_t item, WarpSmem &sm)
+{
+    stepb_item<K, VAR>(J, item, sm);
+}
+
+// The persistent Step B kernel: warps pop (job, item) pairs until the queue is empty.
+__global__ void __launch_bounds__(128) k_stepB_queue(const StepBJob *__restrict__ jobs,
+                                                     const uint2 *__restrict__ items, uint32_t nitems,
+                                                     uint32_t *__restrict__ head)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    QueueSmem &qs = reinterpret_cast<QueueSmem *>(smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    uint32_t cur_job = 0xffffffffu;
+    for (;;) {
+        uint32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(head, 1u);
+        idx = __shfl_sync(FULL, idx, 0);
+        if (idx >= nitems) break;
+        const uint2 it = items[idx];
+        if (it.x != cur_job) {   // stage the job description in shared memory
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(jobs + it.x);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&qs.job);
+            for (uint32_t w = lane; w < sizeof(StepBJob) / 4; w += 32) dst[w] = src[w];
+            cur_job = it.x;
+            __syncwarp();
+        }
+        const StepBJob &J = qs.job;
+        switch (J.K * 4 + J.var) {
+        case 1 * 4 + VAR_BARRETT: queue_item<1, VAR_BARRETT>(J, it.y, qs.w); break;
+        case 2 * 4 + VAR_BARRETT: queue_item<2, VAR_BARRETT>(J, it.y, qs.w); break;
+        case 4 * 4 + VAR_BARRETT: queue_item<4, VAR_BARRETT>(J, it.y, qs.w); break;
+        case 8 * 4 + VAR_BARRETT: queue_item<8, VAR_BARRETT>(J, it.y, qs.w); break;
+        case 1 * 4 + VAR_MONT: queue_item<1, VAR_MONT>(J, it.y, qs.w); break;
+        case 2 * 4 + VAR_MONT: queue_item<2, VAR_MONT>(J, it.y, qs.w); break;
+        case 4 * 4 + VAR_MONT: queue_item<4, VAR_MONT>(J, it.y, qs.w); break;
+        case 8 * 4 + VAR_MONT: queue_item<8, VAR_MONT>(J, it.y, qs.w); break;
+        case 1 * 4 + VAR_FP64: queue_item<1, VAR_FP64>(J, it.y, qs.w); break;
+        case 2 * 4 + VAR_FP64: queue_item<2, VAR_FP64>(J, it.y, qs.w); break;
+        case 4 * 4 + VAR_FP64: queue_item<4, VAR_FP64>(J, it.y, qs.w); break;
+        case 8 * 4 + VAR_FP64: queue_item<8, VAR_FP64>(J, it.y, qs.w); break;
+        default: break;
+        }
+        __syncwarp();
+    }
+}
+
+static constexpr int kQueueWarps = 4;
+
+static size_t queue_smem() { return kQueueWarps * sizeof(QueueSmem); }
+
+static cudaError_t queue_setup(int *blocks_per_sm)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_stepB_queue, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)queue_smem());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_stepB_queue, kQueueWarps * 32,
+                                                         queue_smem());
+}
+
+uint64_t queue_resident_warps()
+{
+    int bps = 0;
+    if (queue_setup(&bps) != cudaSuccess || bps < 1) bps = 1;
+    return (uint64_t)bps * kQueueWarps * num_sms();
+}
+
+// Chooses a job's tiles for a batch whose items should be about `w_target`
+// slot-points each (slot-points = padded terms x points).
+static Tiles batch_tiles(pe_poly *P, uint64_t T, double w_target)
+{
+    Tiles t;
+    t.wpb = kQueueWarps;
+    const TuneEntry *te = tune_lookup(P, T);
+    if (te && te->K <= 8) {
+        t.K = te->K;
+    } else {
+        double best = 1e300;
+        for (uint32_t K : {1u, 2u, 4u, 8u}) {
+            uint64_t nc = 0;
+            for (uint64_t g = 0; g < P->G; ++g) nc += (P->group_off[g + 1] - P->group_off[g] + K - 1) / K;
+            const double c = (double)nc * (K + 0.7);
+            if (c < best * 0.98) {
+                best = c;
+                t.K = K;
+            }
+        }
+    }
+    uint64_t nc = 0;
+    for (uint64_t g = 0; g < P->G; ++g) nc += (P->group_off[g + 1] - P->group_off[g] + t.K - 1) / t.K;
+    const uint64_t slabs = std::max<uint64_t>(1, (nc + 31) / 32);
+    const double one_slab = 32.0 * t.K * (double)T;
+    if (one_slab <= w_target) {
+        t.Tc = (uint32_t)T;
+        t.kslabs = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(slabs, (uint64_t)(w_target / one_slab)));
+    } else {
+        t.kslabs = 1;
+        uint64_t tc = (uint64_t)(w_target / (32.0 * t.K));
+        tc = std::max<uint64_t>(64, (tc + 31) / 32 * 32);
+        t.Tc = (uint32_t)std::min<uint64_t>(tc, T);
+    }
+    return t;
+}
+
+static int resolve_variant(pe_poly *P, uint64_t T) { return run_variant(P, T); }
+
+}  // namespace pe
+
+using namespace pe;
+
+struct pe_batch {
+    std::vector<pe_job> jobs;
+    std::vector<std::vector<uint64_t>> betas;
+    std::vector<size_t> beta_off;      // arena offset of each job's beta
+    DevBuf arena;
+    size_t counters_off = 0, counters_bytes = 0;
+    StepBJob *d_jobs = nullptr;
+    uint2 *d_items = nullptr;
+    PowJob *d_pow = nullptr;
+    uint32_t *d_head = nullptr;
+    uint32_t nitems = 0, njobs_live = 0, max_entries = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int grid = 0;
+    ~pe_batch()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+namespace {
+
+struct Layout {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    }
+};
+
+}  // namespace
+
+extern "C" pe_status poly_eval_batch_plan(const pe_job *jobs, size_t njobs, pe_batch **out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return PE_ERR_ARG;
+    }
+    *out = nullptr;
+    if (njobs && !jobs) {
+        set_error("jobs is NULL");
+        return PE_ERR_ARG;
+    }
+    pe_batch *B = new pe_batch();
+    B->jobs.assign(jobs, jobs + njobs);
+    B->betas.resize(njobs);
+    // Validation and work totals.
+    double w_total = 0.0;
+    for (size_t j = 0; j < njobs; ++j) {
+        const pe_job &jb = jobs[j];
+        if (!jb.poly || (jb.T && jb.poly->G && !jb.out) || jb.T > (1ull << 31)) {
+            set_error("job %zu: NULL poly/out or T above 2^31", j);
+            delete B;
+            return PE_ERR_ARG;
+        }
+        BetaArg ba;
+        pe_status st = check_beta(jb.poly, jb.beta, &ba);
+        if (st != PE_OK) {
+            delete B;
+            return st;
+        }
+        B->betas[j].assign(ba.b, ba.b + jb.poly->E);
+        w_total += (double)jb.poly->s * (double)jb.T;
+    }
+    const uint64_t R = queue_resident_warps();
+    const double w_target = std::max(w_total / (8.0 * (double)R), 32.0 * 64.0);
+    // Per-job plans and arena layout.
+    std::vector<PlanHost> ph(njobs);
+    std::vector<std::vector<uint32_t>> cs(njobs), cg(njobs);
+    std::vector<int> var(njobs);
+    Layout L;
+    const size_t off_jobs = L.take(std::max<size_t>(njobs, 1) * sizeof(StepBJob));
+    const size_t off_pow = L.take(std::max<size_t>(njobs, 1) * sizeof(PowJob));
+    std::vector<size_t> o_cs(njobs), o_cg(njobs), o_unit(njobs), o_span(njobs), o_carry(njobs), o_chain(njobs),
+        o_ptab(njobs), o_cnt(njobs);
+    B->beta_off.resize(njobs);
+    for (size_t j = 0; j < njobs; ++j) {
+        pe_poly *P = jobs[j].poly;
+        if (!jobs[j].T || !P->G) continue;
+        const Tiles t = batch_tiles(P, jobs[j].T, w_target);
+        build_plan_host(P, t, jobs[j].T, ph[j]);
+        cs[j] = P->chunks.cs;
+        cg[j] = P->chunks.cg;
+        var[j] = resolve_variant(P, jobs[j].T);
+        o_cs[j] = L.take(cs[j].size() * 4);
+        o_cg[j] = L.take(std::max<size_t>(cg[j].size(), 1) * 4);
+        o_unit[j] = L.take(ph[j].unit.size() * 4);
+        o_span[j] = L.take(ph[j].span.size() * 4);
+        o_carry[j] = L.take(ph[j].carry_bytes());
+        o_chain[j] = L.take(ph[j].chain_bytes());
+        o_ptab[j] = L.take((size_t)std::max<uint32_t>(P->E, 1) * (P->dmax + 1) * 8);
+        B->beta_off[j] = L.take((size_t)std::max<uint32_t>(P->E, 1) * 8);
+    }
+    // Counters (and the queue head) in one contiguous region, cleared by the graph.
+    B->counters_off = L.off;
+    const size_t off_head = L.take(256);
+    for (size_t j = 0; j < njobs; ++j)
+        if (jobs[j].T && jobs[j].poly->G) o_cnt[j] = L.take(ph[j].counter_bytes());
+    B->counters_bytes = L.off - B->counters_off;
+    // Items, ordered by decreasing cost (a slab-point of a K-term chunk costs K).
+    std::vector<std::pair<double, uint2>> items;
+    for (size_t j = 0; j < njobs; ++j) {
+        if (!jobs[j].T || !jobs[j].poly->G) continue;
+        const PlanHost &p = ph[j];
+        const double lg = std::log2((double)std::max<uint64_t>(2, jobs[j].t0 + jobs[j].T));
+        for (uint32_t q = 0; q < p.Q; ++q) {
+            const uint64_t tc = std::min<uint64_t>(p.Tc, p.T - (uint64_t)q * p.Tc);
+            for (uint32_t u = 0; u < p.U; ++u) {
+                const uint32_t chunks = std::min(p.NC - u * 32 * p.kslabs, 32 * p.kslabs);
+                const double slabs = std::ceil(chunks / 32.0);
+                const double cost = slabs * 32.0 * (p.K * (double)tc * 1.2 + (double)tc * 0.7 + p.K * lg * 3.0);
+                items.push_back({cost, make_uint2((uint32_t)j, q * p.U + u)});
+            }
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    const size_t off_items = L.take(std::max<size_t>(items.size(), 1) * sizeof(uint2));
+    cudaError_t e = B->arena.ensure(L.off);
+    if (e != cudaSuccess) {
+        delete B;
+        return cuda_fail(e, "batch arena");
+    }
+    unsigned char *base = B->arena.as<unsigned char>();
+    std::vector<unsigned char> host(L.off, 0);
+    auto put = [&](size_t off, const void *src, size_t n) {
+        if (n) memcpy(host.data() + off, src, n);
+    };
+    std::vector<StepBJob> hj(njobs);
+    std::vector<PowJob> hp(njobs);
+    for (size_t j = 0; j < njobs; ++j) {
+        const pe_job &jb = jobs[j];
+        pe_poly *P = jb.poly;
+        if (!jb.T || !P->G) continue;
+        put(o_cs[j], cs[j].data(), cs[j].size() * 4);
+        put(o_cg[j], cg[j].data(), cg[j].size() * 4);
+        put(o_unit[j], ph[j].unit.data(), ph[j].unit.size() * 4);
+        put(o_span[j], ph[j].span.data(), ph[j].span.size() * 4);
+        put(B->beta_off[j], B->betas[j].data(), B->betas[j].size() * 8);
+        fill_job(hj[j], P, ph[j], (const uint32_t *)(base + o_cs[j]), (const uint32_t *)(base + o_cg[j]),
+                 (const int32_t *)(base + o_unit[j]), (const uint32_t *)(base + o_span[j]),
+                 (uint32_t *)(base + o_cnt[j]), (ulonglong2 *)(base + o_carry[j]), (ulonglong2 *)(base + o_chain[j]),
+                 jb.t0, jb.out, nullptr, (const uint64_t *)(base + o_ptab[j]), var[j]);
+        hp[j].beta = (const uint64_t *)(base + B->beta_off[j]);
+        hp[j].ptab = (uint64_t *)(base + o_ptab[j]);
+        hp[j].E = P->E;
+        hp[j].dp1 = P->dmax + 1;
+        hp[j].mc = P->mc;
+        B->max_entries = std::max(B->max_entries, P->E * (P->dmax + 1));
+    }
+    put(off_jobs, hj.data(), njobs * sizeof(StepBJob));
+    put(off_pow, hp.data(), njobs * sizeof(PowJob));
+    std::vector<uint2> it(items.size());
+    for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
+    put(off_items, it.data(), it.size() * sizeof(uint2));
+    if ((e = cudaMemcpy(base, host.data(), L.off, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        delete B;
+        return cuda_fail(e, "batch upload");
+    }
+    B->d_jobs = (StepBJob *)(base + off_jobs);
+    B->d_pow = (PowJob *)(base + off_pow);
+    B->d_items = (uint2 *)(base + off_items);
+    B->d_head = (uint32_t *)(base + off_head);
+    B->nitems = (uint32_t)items.size();
+    B->njobs_live = (uint32_t)njobs;
+    int bps = 0;
+    if ((e = queue_setup(&bps)) != cudaSuccess) {
+        delete B;
+        return cuda_fail(e, "queue kernel setup");
+    }
+    B->grid = std::max(1, bps) * num_sms();
+    // Capture the batch as a CUDA graph on a private stream.
+    if ((e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        delete B;
+        return cuda_fail(e, "graph capture");
+    }
+    cudaMemsetAsync(base + B->counters_off, 0, B->counters_bytes, B->cap);
+    if (B->max_entries && njobs)
+        k_powtab_batch<<<dim3((B->max_entries + 127) / 128, (unsigned)njobs), 128, 0, B->cap>>>(B->d_pow);
+    if (B->nitems)
+        k_stepB_queue<<<B->grid, kQueueWarps * 32, queue_smem(), B->cap>>>(B->d_jobs, B->d_items, B->nitems,
+                                                                           B->d_head);
+    cudaError_t le = cudaGetLastError();
+    e = cudaStreamEndCapture(B->cap, &B->graph);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
+    if (e != cudaSuccess) {
+        delete B;
+        return cuda_fail(e, "graph build");
+    }
+    *out = B;
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_batch_launch(pe_batch *B, void *stream)
+{
+    if (!B) {
+        set_error("NULL batch");
+        return PE_ERR_ARG;
+    }
+    cudaError_t e = cudaGraphLaunch(B->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_batch_set_beta(pe_batch *B, size_t j, const uint64_t *beta)
+{
+    if (!B || j >= B->jobs.size()) {
+        set_error("bad batch or job index");
+        return PE_ERR_ARG;
+    }
+    BetaArg ba;
+    pe_status st = check_beta(B->jobs[j].poly, beta, &ba);
+    if (st != PE_OK) return st;
+    const uint32_t E = B->jobs[j].poly->E;
+    if (!E) return PE_OK;
+    B->betas[j].assign(ba.b, ba.b + E);
+    cudaError_t e = cudaMemcpy(B->arena.as<unsigned char>() + B->beta_off[j], B->betas[j].data(), E * 8,
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "beta upload");
+    return PE_OK;
+}
+
+extern "C" void poly_eval_batch_destroy(pe_batch *B) { delete B; }
+
+extern "C" pe_status poly_eval_batch(const pe_job *jobs, size_t njobs, void *stream)
+{
+    pe_batch *B = nullptr;
+    pe_status st = poly_eval_batch_plan(jobs, njobs, &B);
+    if (st != PE_OK) return st;
+    st = poly_eval_batch_launch(B, stream);
+    if (st == PE_OK) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "batch");
+    }
+    poly_eval_batch_destroy(B);
+    return st;
+}

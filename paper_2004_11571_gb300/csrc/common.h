@@ -44,6 +44,7 @@ struct StepBJob {
     uint64_t s, T, t0, G;
     uint32_t NC, U, Q, kslabs, Tc;
     uint32_t E, dp1, exp_bytes;
+    uint32_t K, var;          // lane chunk size and modular product (queue dispatch)
     ModCtx mc;
 };
 

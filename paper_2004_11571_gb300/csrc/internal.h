@@ -44,8 +44,22 @@ struct DevBuf {
     T *as() const { return reinterpret_cast<T *>(p); }
 };
 
+// Host side of a Step B work decomposition: units of kslabs slabs, T-chunks
+// of Tc points, and the groups that cross unit boundaries ("spans").
+struct PlanHost {
+    uint32_t K = 0, kslabs = 0, Tc = 0, wpb = 0;
+    uint64_t T = 0;
+    uint32_t NC = 0, U = 0, Q = 0, S = 0, nslots = 0;
+    std::vector<int32_t> unit;    // 4U: lslot, rslot, lspan, rspan
+    std::vector<uint32_t> span;   // 3*max(S,1): group, slot base, slot count
+    size_t counter_bytes() const;
+    size_t carry_bytes() const;
+    size_t chain_bytes() const;
+};
+
 // Work decomposition of Step B for one (polynomial, tile shape, T).
 struct Plan {
+    PlanHost host;
     bool valid = false;
     uint32_t K = 0, kslabs = 0, Q = 0, Tc = 0, wpb = 0;
     uint64_t T = 0;
@@ -70,7 +84,8 @@ struct pe_poly {
     uint64_t p = 0;
     uint32_t n = 0, E = 0;
     uint64_t s = 0, G = 0;
-    int variant = 0;             // resolved pe_variant
+    int variant = 0;             // variant of the current plan
+    int requested_variant = 0;   // as created (PE_MODMUL_AUTO: tuner's choice, else Barrett)
     pe::ModCtx mc{};
     uint32_t exp_bytes = 1;      // 1 or 2 on the device
     uint32_t dmax = 0;           // max exponent over x3..xn
@@ -100,6 +115,11 @@ int num_sms();
 Tiles choose_tiles(pe_poly *poly, uint64_t T, const pe_tiles *forced);
 // Builds (or reuses) the plan for the given tiles and T.
 pe_status ensure_plan(pe_poly *poly, const Tiles &t, uint64_t T);
+void build_chunks(pe_poly *P, uint32_t K);
+void build_plan_host(pe_poly *P, const Tiles &t, uint64_t T, PlanHost &ph);
+void fill_job(StepBJob &J, pe_poly *P, const PlanHost &ph, const uint32_t *cs, const uint32_t *cg,
+              const int32_t *unit, const uint32_t *span, uint32_t *counters, ulonglong2 *carry, ulonglong2 *chain,
+              uint64_t t0, uint64_t *out_dev, const uint64_t *mR, const uint64_t *ptab, int variant);
 // Fills a Step B job description from a poly and its current plan.
 StepBJob make_job(pe_poly *poly, uint64_t T, uint64_t t0, uint64_t *out_dev, bool fused);
 pe_status check_beta(const pe_poly *poly, const uint64_t *beta, BetaArg *arg);

@@ -50,6 +50,19 @@ __device__ __forceinline__ uint64_t barrett_mul(uint64_t x, uint64_t w, uint64_t
     return x * w - __umul64hi(x, wq) * p;
 }
 
+// The same product with a cheaper quotient: with x = x1*2^32 + x0 and
+// wq = w1*2^32 + w0, x*wq = (x1*w1 + hi(x1*w0) + hi(x0*w1)) * 2^64 + R with
+// 0 <= R < 3 * 2^64, so the estimate below is floor(x*wq / 2^64) minus 0, 1
+// or 2.  The result therefore lies in [0, 4p), exact in 64 bits for
+// p < 2^62, and stays a valid input (any x < 2^64) for the next product.
+__device__ __forceinline__ uint64_t barrett_mul_lazy4(uint64_t x, uint64_t w, uint64_t wq, uint64_t p)
+{
+    const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+    const uint32_t w0 = (uint32_t)wq, w1 = (uint32_t)(wq >> 32);
+    const uint64_t q = (uint64_t)x1 * w1 + __umulhi(x1, w0) + __umulhi(x0, w1);
+    return x * w - q * p;
+}
+
 // Given mR = m * 2^64 mod p (canonical), the Barrett quotient of m is
 // (m*2^64 - mR) / p, an exact division, hence equal to -mR * p^-1 mod 2^64.
 __device__ __forceinline__ uint64_t barrett_quotient_from_mont(uint64_t mR, const ModCtx &mc)

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256) k_stepB(StepBJob J, uint32_t nitems)
     const uint32_t warp = threadIdx.x >> 5;
     const uint32_t item = blockIdx.x * (blockDim.x >> 5) + warp;
     if (item >= nitems) return;
-    stepb_item<K, VAR, false>(J, item, sm[warp]);
+    stepb_item<K, VAR>(J, item, sm[warp]);
 }
 
 cudaError_t launch_powtab(const BetaArg &beta, uint32_t E, uint32_t dp1, const ModCtx &mc, uint64_t *ptab,

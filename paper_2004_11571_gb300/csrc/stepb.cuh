@@ -96,7 +96,7 @@ __device__ __forceinline__ void lane_point(Lane<VAR> (&st)[K], const ModCtx &mc,
         for (int k = 0; k < K; ++k) {
             add96(lo, hi, st[k].v);
             if constexpr (VAR == VAR_BARRETT)
-                st[k].v = barrett_mul(st[k].v, st[k].w, st[k].wq, mc.p);
+                st[k].v = barrett_mul_lazy4(st[k].v, st[k].w, st[k].wq, mc.p);
             else
                 st[k].v = mont_mul(st[k].v, st[k].y, mc);
         }
@@ -137,7 +137,9 @@ __device__ __forceinline__ void close_group(const StepBJob &J, uint64_t row, uin
         J.out[row * J.G + g] = reduce96(lo, hi, J.mc);
 }
 
-template <int K, int VAR, bool FUSED_A>
+// Step A is fused (m_i computed from the exponents and power tables) when the
+// job has no precomputed monomial array.
+template <int K, int VAR>
 __device__ __forceinline__ void stepb_item(const StepBJob &J, uint32_t item, WarpSmem &sm)
 {
     const unsigned FULL = 0xffffffffu;
@@ -170,9 +172,7 @@ __device__ __forceinline__ void stepb_item(const StepBJob &J, uint32_t item, War
             if ((uint32_t)k < cnt) {
                 const uint64_t i = (uint64_t)start + k;
                 const uint64_t a = J.coeffs[i];
-                uint64_t mR;
-                if constexpr (FUSED_A) mR = fused_monomial(J, i);
-                else mR = J.mR[i];
+                const uint64_t mR = J.mR ? J.mR[i] : fused_monomial(J, i);
                 const uint64_t v0 = canon(mont_mul(a, mont_pow(mR, e, mc), mc), mc.p);
                 st[k].init(v0, mR, mc);
             } else {

@@ -1,0 +1,108 @@
+"""Batched evaluation (one persistent kernel, device work queue, CUDA graph)
+is bit-exact against the oracle and against the plain path (GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2004_11571_gb300 as pe  # noqa: E402
+
+
+def _mixed(count, seed, s_max=30_000):
+    ws = wl.config_batched(seed=seed, count=count, s_min=200, s_max=s_max)
+    return ws
+
+
+def test_batch_matches_oracle_and_plain():
+    ws = _mixed(24, 77)
+    variants = ["auto", "barrett64", "mont64"]
+    polys, outs, jobs = [], [], []
+    for k, w in enumerate(ws):
+        v = variants[k % 3]
+        if k % 4 == 0 and w.p < (1 << 50):
+            v = "fp64"
+        poly = pe.Poly.from_workload(w, variant=v)
+        out = torch.full((w.T, poly.G), -1, dtype=torch.int64, device="cuda")
+        t0 = [1, 0, 17, 1 << 33][k % 4]
+        polys.append((poly, t0))
+        outs.append(out)
+        jobs.append((poly, w.beta, w.T, t0, out))
+    batch = pe.Batch(jobs)
+    for rep in range(2):                      # the graph is re-launchable
+        for o in outs:
+            o.fill_(-1)
+        batch.launch()
+        torch.cuda.synchronize()
+        for k, w in enumerate(ws):
+            poly, t0 = polys[k]
+            got = pe.to_u64(outs[k])
+            if w.s * w.T <= 3_000_000:
+                keys, ref = oracle.eval_direct(w, t0=t0)
+                assert np.array_equal(poly.groups(), keys)
+                assert np.array_equal(got, ref), f"job {k}"
+            else:
+                ref = pe.to_u64(poly.run(w.beta, w.T, t0))
+                assert np.array_equal(got, ref), f"job {k}"
+                cells = oracle.CellOracle(w)
+                rnd = np.random.default_rng(k)
+                r = rnd.integers(0, w.T, 8)
+                g = rnd.integers(0, cells.G, 8)
+                assert np.array_equal(got[r, g], cells(r + t0, g))
+    # new beta for one job
+    w = ws[3]
+    nb = wl._uniform_mod(np.random.default_rng(5), w.p, w.n - 2, lo=2)
+    batch.set_beta(3, nb)
+    batch.launch()
+    torch.cuda.synchronize()
+    w2 = wl.Workload(p=w.p, n=w.n, coeffs=w.coeffs, exps=w.exps, beta=nb, T=w.T, t0=polys[3][1])
+    ref = pe.to_u64(polys[3][0].run(nb, w.T, polys[3][1]))
+    assert np.array_equal(pe.to_u64(outs[3]), ref)
+    batch.close()
+
+
+def test_batch_edge_jobs():
+    p = wl.random_prime(62, 88)
+    ws = [wl.make_uniform(n=6, s=1, p=p, deg12=2, deg_rest=3, T=3, seed=1),
+          wl.make_uniform(n=2, s=500, p=p, deg12=5, deg_rest=0, T=40, seed=2),
+          wl.make_uniform(n=6, s=800, p=p, deg12=0, deg_rest=4, T=1, seed=3),
+          wl.make_uniform(n=9, s=7000, p=p, deg12=60, deg_rest=10, T=70, seed=4)]
+    jobs, outs = [], []
+    for w in ws:
+        poly = pe.Poly.from_workload(w)
+        out = torch.full((w.T, poly.G), -1, dtype=torch.int64, device="cuda")
+        jobs.append((poly, w.beta, w.T, 1, out))
+        outs.append(out)
+    batch = pe.Batch(jobs)
+    batch.launch()
+    torch.cuda.synchronize()
+    for w, o in zip(ws, outs):
+        _, ref = oracle.eval_direct(w)
+        assert np.array_equal(pe.to_u64(o), ref)
+    batch.close()
+    assert pe.Batch([]) is not None
+
+
+def test_tuner_records_and_plain_uses_it(tmp_path):
+    w = wl.make_zipf(n=7, s=60_000, p=wl.random_prime(62, 90), deg12=20, deg_rest=9, T=256, seed=9)
+    poly = pe.Poly.from_workload(w)
+    tiles, ms = pe.tune(poly, w.T)
+    assert tiles["K"] in (1, 2, 4, 8, 16) and ms > 0
+    path = str(tmp_path / "tune.jsonl")
+    pe.tune_save(path)
+    pe.tune_load(path)
+    assert "key" in open(path).read()
+    _, ref = oracle.eval_direct(wl.Workload(p=w.p, n=w.n, coeffs=w.coeffs, exps=w.exps, beta=w.beta, T=8))
+    got = pe.to_u64(poly.run(w.beta, 8))
+    assert np.array_equal(got, ref)
+    got = pe.to_u64(poly.run(w.beta, w.T))
+    cells = oracle.CellOracle(w)
+    rnd = np.random.default_rng(0)
+    r, g = rnd.integers(0, w.T, 16), rnd.integers(0, cells.G, 16)
+    assert np.array_equal(got[r, g], cells(r + 1, g))
