@@ -155,6 +155,8 @@ typedef struct {
     uint32_t slabs;           /* slabs per work item */
     uint32_t tchunk;          /* points per work item */
     uint32_t warps_per_block; /* 1..8 */
+    uint32_t tail;            /* with slabs and tchunk forced: final points run as a band of
+                                 one-slab items issued after the others (0: none) */
 } pe_tiles;
 
 /* Forces tile parameters for later runs of this handle (NULL = automatic). */
@@ -168,6 +170,7 @@ typedef struct {
     uint64_t items;           /* warp work items per run */
     uint64_t spans;           /* groups whose terms cross work-item boundaries */
     uint64_t padded_terms;    /* chunks * K */
+    uint64_t tail_points;     /* last points run as one-slab items after the others (0: none) */
 } pe_plan_info;
 
 pe_status poly_eval_plan_info(pe_poly *poly, uint64_t T, pe_plan_info *info);

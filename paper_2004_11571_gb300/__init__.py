@@ -51,12 +51,13 @@ class _Desc(ctypes.Structure):
 
 class _Tiles(ctypes.Structure):
     _fields_ = [("K", ctypes.c_uint32), ("slabs", ctypes.c_uint32), ("tchunk", ctypes.c_uint32),
-                ("warps_per_block", ctypes.c_uint32)]
+                ("warps_per_block", ctypes.c_uint32), ("tail", ctypes.c_uint32)]
 
 
 class _PlanInfo(ctypes.Structure):
     _fields_ = [("tiles", _Tiles), ("variant", ctypes.c_int), ("chunks", ctypes.c_uint64),
-                ("items", ctypes.c_uint64), ("spans", ctypes.c_uint64), ("padded_terms", ctypes.c_uint64)]
+                ("items", ctypes.c_uint64), ("spans", ctypes.c_uint64), ("padded_terms", ctypes.c_uint64),
+                ("tail_points", ctypes.c_uint64)]
 
 
 class _Job(ctypes.Structure):
@@ -235,8 +236,8 @@ class Poly:
         _check(lib().poly_eval_run(self._h, bptr, int(T), int(t0), ptr, _stream_ptr(stream)))
         return out
 
-    def set_tiles(self, K=0, slabs=0, tchunk=0, warps_per_block=0):
-        t = _Tiles(K, slabs, tchunk, warps_per_block)
+    def set_tiles(self, K=0, slabs=0, tchunk=0, warps_per_block=0, tail=0):
+        t = _Tiles(K, slabs, tchunk, warps_per_block, tail)
         _check(lib().poly_eval_set_tiles(self._h, ctypes.byref(t)))
 
     def plan_info(self, T: int) -> dict:
@@ -245,7 +246,7 @@ class Poly:
         return {"K": info.tiles.K, "slabs": info.tiles.slabs, "tchunk": info.tiles.tchunk,
                 "warps_per_block": info.tiles.warps_per_block, "variant": info.variant,
                 "chunks": info.chunks, "items": info.items, "spans": info.spans,
-                "padded_terms": info.padded_terms}
+                "padded_terms": info.padded_terms, "tail_points": info.tail_points}
 
     def launches_per_run(self, T: int) -> int:
         n = ctypes.c_uint32()

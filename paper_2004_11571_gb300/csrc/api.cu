@@ -84,21 +84,14 @@ static uint64_t count_chunks(const pe_poly *P, uint32_t K)
     return nc;
 }
 
-double estimate_cost(uint64_t NC, uint32_t K, uint32_t kslabs, uint64_t Tc, uint64_t T, uint64_t R)
-{
-    const uint64_t slabs = (NC + 31) / 32;
-    const uint64_t U = (slabs + kslabs - 1) / kslabs;
-    const uint64_t Q = (T + Tc - 1) / Tc;
-    const uint64_t items = U * Q;
-    const uint64_t waves = (items + R - 1) / R;
-    // Per lane and point: K products+sums (~17 instructions each) plus the
-    // transposed walk (~12).  Jump start: ~2 log2(t) Montgomery products of
-    // ~22 instructions for each of the K terms, once per slab and T-chunk.
-    const double lg = Q > 1 ? std::log2((double)T) : 0.0;
-    const double per_slab = (double)Tc * (17.0 * K + 12.0) + (Q > 1 ? 44.0 * K * lg : 4.0 * K * 22.0);
-    return (double)waves * kslabs * per_slab;
-}
+// Tail band shape for `tail` final points: one-slab items of at most 64 points.
+static uint32_t tail_tc(uint64_t tail) { return (uint32_t)std::min<uint64_t>(tail, 64); }
 
+// Tile shape.  Items are issued in order and each warp takes the next, so the
+// run ends unevenly by about one item; measured on GB300, items of about 2% of
+// a warp's share of the work (at least 128 slab-points, at most 512 points)
+// balance that against the fixed cost of starting an item.  Small jobs use
+// smaller items so that every warp gets one.
 Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
 {
     Tiles t;
@@ -121,35 +114,32 @@ Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
             }
         }
     }
+    if (f && f->slabs && f->tchunk) {
+        t.kslabs = f->slabs;
+        t.tailT = f->tail && f->tail < T ? f->tail : 0;
+        t.Tc = (uint32_t)std::min<uint64_t>(f->tchunk, T - t.tailT);
+        return t;
+    }
     const uint64_t NC = count_chunks(P, t.K);
     int bps = 0;
     if (stepB_occupancy((int)t.K, P->variant, (int)t.wpb, &bps) != cudaSuccess || bps <= 0) bps = 1;
     const uint64_t R = (uint64_t)bps * t.wpb * num_sms();
-    if (f && f->slabs && f->tchunk) {
-        t.kslabs = f->slabs;
-        t.Tc = (uint32_t)std::min<uint64_t>(f->tchunk, T);
-        return t;
-    }
-    double best = 1e300;
-    const uint64_t slabs = (NC + 31) / 32;
-    const uint32_t qmax = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(64, T / 32));
-    for (uint32_t Q = 1; Q <= qmax; ++Q) {
-        const uint64_t Tc = (T + Q - 1) / Q;
-        if (f && f->tchunk && Tc != std::min<uint64_t>(f->tchunk, T)) continue;
-        for (uint32_t k = 1; k <= 64 && k <= std::max<uint64_t>(1, slabs); ++k) {
-            if (f && f->slabs && k != f->slabs) continue;
-            const double c = estimate_cost(NC, t.K, k, Tc, T, R);
-            if (c < best * 0.999) {
-                best = c;
-                t.kslabs = k;
-                t.Tc = (uint32_t)Tc;
-            }
-        }
-    }
-    if (!t.kslabs) {
-        t.kslabs = f && f->slabs ? f->slabs : 1;
-        t.Tc = (uint32_t)std::min<uint64_t>(f && f->tchunk ? f->tchunk : T, T);
-    }
+    const uint64_t slabs = std::max<uint64_t>(1, (NC + 31) / 32);
+    // Start rows are limited by kMaxStarts and by 1 GB of starting values.
+    const uint64_t lmax = std::max<uint64_t>(
+        1, std::min<uint64_t>(kMaxStarts, (1ull << 30) / (8 * std::max<uint64_t>(P->s, 1))));
+    const double per_warp = (double)slabs * (double)T / (double)R;
+    double target = std::max(128.0, 0.02 * per_warp);                 // slab-points per item
+    if ((double)slabs * (double)T < target * (double)R)               // small job: one item per warp
+        target = std::max(32.0, (double)slabs * (double)T / (double)R);
+    uint64_t Tc = f && f->tchunk ? f->tchunk : (uint64_t)std::min<double>(512.0, target);
+    Tc = std::max<uint64_t>(1, std::min<uint64_t>(Tc, T));
+    Tc = std::max<uint64_t>(Tc, (T + lmax - 1) / lmax);               // start-row limit
+    uint64_t k = f && f->slabs ? f->slabs : (uint64_t)std::max(1.0, std::floor(target / (double)Tc));
+    k = std::max<uint64_t>(1, std::min<uint64_t>(k, slabs));
+    t.kslabs = (uint32_t)k;
+    t.Tc = (uint32_t)Tc;
+    t.tailT = 0;
     return t;
 }
 
@@ -257,9 +247,8 @@ void fill_job(StepBJob &J, pe_poly *P, const PlanHost &ph, const uint32_t *cs, c
     J.mc = P->mc;
 }
 
-pe_status ensure_plan(pe_poly *P, const Tiles &t, uint64_t T)
+pe_status ensure_plan(pe_poly *P, Plan &pl, const Tiles &t, uint64_t T)
 {
-    Plan &pl = P->plan;
     if (pl.valid && pl.K == t.K && pl.kslabs == t.kslabs && pl.Tc == t.Tc && pl.T == T && pl.wpb == t.wpb)
         return PE_OK;
     pl.valid = false;
@@ -294,15 +283,13 @@ pe_status ensure_plan(pe_poly *P, const Tiles &t, uint64_t T)
     return PE_OK;
 }
 
-StepBJob make_job(pe_poly *P, uint64_t T, uint64_t t0, uint64_t *out_dev, bool fused)
+StepBJob make_job(pe_poly *P, const Plan &pl, uint64_t t0, uint64_t *out_dev, bool fused)
 {
-    const Plan &pl = P->plan;
     StepBJob J;
     fill_job(J, P, pl.host, pl.cs.as<uint32_t>(), pl.cg.as<uint32_t>(), pl.unit.as<int32_t>(),
              pl.span.as<uint32_t>(), pl.counters.as<uint32_t>(), pl.carry.as<ulonglong2>(),
              pl.chain.as<ulonglong2>(), t0, out_dev, fused ? nullptr : P->mR.as<uint64_t>(),
              P->ptab.as<uint64_t>(), P->variant);
-    (void)T;
     return J;
 }
 
@@ -501,6 +488,7 @@ extern "C" pe_status poly_eval_set_tiles(pe_poly *P, const pe_tiles *t)
     }
     P->forced = *t;
     P->plan.valid = false;
+    P->tail_plan.valid = false;
     return PE_OK;
 }
 
@@ -510,9 +498,20 @@ static pe_status plan_for(pe_poly *P, uint64_t T, Tiles *tiles)
     if (v != P->variant) {
         P->variant = v;
         P->plan.valid = false;
+        P->tail_plan.valid = false;
     }
     *tiles = choose_tiles(P, T, &P->forced);
-    return ensure_plan(P, *tiles, T);
+    if (P->tailT != tiles->tailT) {
+        P->plan.valid = false;
+        P->tail_plan.valid = false;
+        P->tailT = tiles->tailT;
+    }
+    pe_status st = ensure_plan(P, P->plan, *tiles, T - tiles->tailT);
+    if (st != PE_OK || !tiles->tailT) return st;
+    Tiles tt = *tiles;
+    tt.kslabs = 1;
+    tt.Tc = tail_tc(tiles->tailT);
+    return ensure_plan(P, P->tail_plan, tt, tiles->tailT);
 }
 
 extern "C" pe_status poly_eval_plan_info(pe_poly *P, uint64_t T, pe_plan_info *info)
@@ -531,9 +530,10 @@ extern "C" pe_status poly_eval_plan_info(pe_poly *P, uint64_t T, pe_plan_info *i
     info->tiles.warps_per_block = t.wpb;
     info->variant = (pe_variant)P->variant;
     info->chunks = P->plan.NC;
-    info->items = (uint64_t)P->plan.U * P->plan.Q;
+    info->items = (uint64_t)P->plan.U * P->plan.Q + (t.tailT ? (uint64_t)P->tail_plan.U * P->tail_plan.Q : 0);
     info->spans = P->plan.S;
     info->padded_terms = (uint64_t)P->plan.NC * t.K;
+    info->tail_points = t.tailT;
     return PE_OK;
 }
 
@@ -637,12 +637,37 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
     if ((e = launch_powtab(barg, P->E, dp1, P->mc, P->ptab.as<uint64_t>(), cs)) != cudaSuccess)
         return cuda_fail(e, "power tables");
     mark(1);
-    if ((e = launch_stepA(P->exps.p, P->exp_bytes, P->s, P->E, P->ptab.as<uint64_t>(), dp1, P->mc,
-                          P->mR.as<uint64_t>(), num_sms(), cs)) != cudaSuccess)
-        return cuda_fail(e, "Step A");
-    const StepBJob J = make_job(P, T, t0, out_dev, false);
+    // Item start rows: band 0's T-chunks, then the tail band's.
+    const uint64_t T0 = T - t.tailT;
+    StartRows sr{};
+    const uint32_t q0 = P->plan.Q, q1 = t.tailT ? P->tail_plan.Q : 0;
+    const bool use_starts = q0 + q1 <= (uint32_t)kMaxStarts;
+    if (use_starts) {
+        for (uint32_t q = 0; q < q0; ++q) sr.row[sr.n++] = q * P->plan.Tc;
+        for (uint32_t q = 0; q < q1; ++q) sr.row[sr.n++] = (uint32_t)T0 + q * P->tail_plan.Tc;
+        if ((e = P->vstart.ensure((size_t)sr.n * P->s * 8)) != cudaSuccess) return cuda_fail(e, "start values");
+        e = launch_stepA_starts(P->exps.p, P->exp_bytes, P->coeffs.as<uint64_t>(), P->s, P->E,
+                                P->ptab.as<uint64_t>(), dp1, P->mc, t0, sr, P->mR.as<uint64_t>(),
+                                P->vstart.as<uint64_t>(), num_sms(), cs);
+    } else {
+        e = launch_stepA(P->exps.p, P->exp_bytes, P->s, P->E, P->ptab.as<uint64_t>(), dp1, P->mc,
+                         P->mR.as<uint64_t>(), num_sms(), cs);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "Step A");
+    StepBJob J0 = make_job(P, P->plan, t0, out_dev, false);
+    StepBJob J1{};
+    uint32_t n1 = 0;
+    if (t.tailT) {
+        J1 = make_job(P, P->tail_plan, t0 + T0, out_dev + T0 * P->G, false);
+        n1 = P->tail_plan.U * P->tail_plan.Q;
+    }
+    if (use_starts) {
+        J0.vstart = J1.vstart = P->vstart.as<uint64_t>();
+        J0.vs_base = 0;
+        J1.vs_base = q0;
+    }
     mark(2);
-    if ((e = launch_stepB((int)t.K, P->variant, J, P->plan.U * P->plan.Q, (int)t.wpb, cs)) != cudaSuccess)
+    if ((e = launch_stepB((int)t.K, P->variant, J0, P->plan.U * P->plan.Q, J1, n1, (int)t.wpb, cs)) != cudaSuccess)
         return cuda_fail(e, "Step B");
     mark(3);
     if (!dev_out) {

@@ -45,7 +45,17 @@ struct StepBJob {
     uint32_t NC, U, Q, kslabs, Tc;
     uint32_t E, dp1, exp_bytes;
     uint32_t K, var;          // lane chunk size and modular product (queue dispatch)
+    const uint64_t *vstart;   // L x s starting values a_i m_i^t per item start row, or nullptr (jump start)
+    uint32_t vs_base;         // row of vstart used by T-chunk 0 of this job
     ModCtx mc;
+};
+
+constexpr int kMaxStarts = 128;
+
+// Start rows (offsets from t0) of the work items of a plain run.
+struct StartRows {
+    uint32_t n;
+    uint32_t row[kMaxStarts];
 };
 
 }  // namespace pe

@@ -76,6 +76,7 @@ struct HostChunks {
 
 struct Tiles {
     uint32_t K = 0, kslabs = 0, Tc = 0, wpb = 0;
+    uint32_t tailT = 0;   // points in the tail band of one-slab items (0: none)
 };
 
 }  // namespace pe
@@ -91,9 +92,11 @@ struct pe_poly {
     uint32_t dmax = 0;           // max exponent over x3..xn
     std::vector<uint64_t> group_off;   // G+1 (host)
     std::vector<uint32_t> keys;        // 2G (host)
-    pe::DevBuf coeffs, exps, mR, ptab, out_scratch;
+    pe::DevBuf coeffs, exps, mR, ptab, out_scratch, vstart;
     pe::HostChunks chunks;
-    pe::Plan plan;
+    pe::Plan plan;        // band of large items: rows [0, T - tail)
+    pe::Plan tail_plan;   // band of small items: the last tail rows
+    uint32_t tailT = 0;
     pe_tiles forced{};
     bool timing = false;
     std::vector<cudaEvent_t> events;   // 4 per timed run
@@ -104,8 +107,9 @@ struct pe_poly {
     }
     uint64_t device_bytes() const
     {
-        return coeffs.bytes + exps.bytes + mR.bytes + ptab.bytes + out_scratch.bytes + plan.cs.bytes +
-               plan.cg.bytes + plan.unit.bytes + plan.span.bytes + plan.scratch_bytes();
+        return coeffs.bytes + exps.bytes + mR.bytes + ptab.bytes + out_scratch.bytes + vstart.bytes + plan.cs.bytes +
+               plan.cg.bytes + plan.unit.bytes + plan.span.bytes + plan.scratch_bytes() + tail_plan.cs.bytes +
+               tail_plan.cg.bytes + tail_plan.unit.bytes + tail_plan.span.bytes + tail_plan.scratch_bytes();
     }
 };
 
@@ -113,16 +117,14 @@ namespace pe {
 int num_sms();
 // Chooses the tile shape for a run of T points (forced fields win).
 Tiles choose_tiles(pe_poly *poly, uint64_t T, const pe_tiles *forced);
-// Builds (or reuses) the plan for the given tiles and T.
-pe_status ensure_plan(pe_poly *poly, const Tiles &t, uint64_t T);
+// Builds (or reuses) `pl` for the given tiles and T.
+pe_status ensure_plan(pe_poly *poly, Plan &pl, const Tiles &t, uint64_t T);
 void build_chunks(pe_poly *P, uint32_t K);
 void build_plan_host(pe_poly *P, const Tiles &t, uint64_t T, PlanHost &ph);
 void fill_job(StepBJob &J, pe_poly *P, const PlanHost &ph, const uint32_t *cs, const uint32_t *cg,
               const int32_t *unit, const uint32_t *span, uint32_t *counters, ulonglong2 *carry, ulonglong2 *chain,
               uint64_t t0, uint64_t *out_dev, const uint64_t *mR, const uint64_t *ptab, int variant);
 // Fills a Step B job description from a poly and its current plan.
-StepBJob make_job(pe_poly *poly, uint64_t T, uint64_t t0, uint64_t *out_dev, bool fused);
+StepBJob make_job(pe_poly *poly, const Plan &pl, uint64_t t0, uint64_t *out_dev, bool fused);
 pe_status check_beta(const pe_poly *poly, const uint64_t *beta, BetaArg *arg);
-// Cost model of one tile shape (relative time units), used by choose_tiles and the batch planner.
-double estimate_cost(uint64_t NC, uint32_t K, uint32_t kslabs, uint64_t Tc, uint64_t T, uint64_t R);
 }  // namespace pe

@@ -9,7 +9,11 @@ cudaError_t launch_powtab(const BetaArg &beta, uint32_t E, uint32_t dp1, const M
                           cudaStream_t st);
 cudaError_t launch_stepA(const void *exps, uint32_t exp_bytes, uint64_t s, uint32_t E, const uint64_t *ptab,
                          uint32_t dp1, const ModCtx &mc, uint64_t *mR, int num_sms, cudaStream_t st);
-cudaError_t launch_stepB(int K, int var, const StepBJob &J, uint32_t nitems, int wpb, cudaStream_t st);
+cudaError_t launch_stepA_starts(const void *exps, uint32_t exp_bytes, const uint64_t *coeffs, uint64_t s, uint32_t E,
+                               const uint64_t *ptab, uint32_t dp1, const ModCtx &mc, uint64_t t0, const StartRows &sr,
+                               uint64_t *mR, uint64_t *vstart, int num_sms, cudaStream_t st);
+cudaError_t launch_stepB(int K, int var, const StepBJob &J0, uint32_t n0, const StepBJob &J1, uint32_t n1, int wpb,
+                         cudaStream_t st);
 cudaError_t stepB_occupancy(int K, int var, int wpb, int *blocks_per_sm);
 
 }  // namespace pe

@@ -29,16 +29,49 @@ __global__ void k_stepA(const ExpT *__restrict__ exps, uint64_t s, uint32_t E, c
         mR[i] = monomial_mont(exps, s, i, E, ptab, dp1, mc);
 }
 
+// Step A with starting values: besides m_i, every term's value a_i * m_i^t
+// at each work-item start row t = t0 + row[k], so that Step B items start
+// with one load.  Consecutive rows are reached by multiplying by m_i^gap,
+// with m_i^gap recomputed only when the gap changes.
+template <typename ExpT>
+__global__ void k_stepA_starts(const ExpT *__restrict__ exps, const uint64_t *__restrict__ coeffs, uint64_t s,
+                               uint32_t E, const uint64_t *__restrict__ ptab, uint32_t dp1, ModCtx mc, uint64_t t0,
+                               StartRows sr, uint64_t *__restrict__ mR_out, uint64_t *__restrict__ vstart)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t mR = monomial_mont(exps, s, i, E, ptab, dp1, mc);
+        mR_out[i] = mR;
+        uint64_t cur = canon(mont_mul(coeffs[i], mont_pow(mR, t0 + sr.row[0], mc), mc), mc.p);
+        vstart[i] = cur;
+        uint32_t prev_gap = 0;
+        uint64_t gapR = mc.r1;
+        for (uint32_t k = 1; k < sr.n; ++k) {
+            const uint32_t gap = sr.row[k] - sr.row[k - 1];
+            if (gap != prev_gap) {
+                gapR = mont_pow(mR, gap, mc);
+                prev_gap = gap;
+            }
+            cur = canon(mont_mul(cur, gapR, mc), mc.p);
+            vstart[(uint64_t)k * s + i] = cur;
+        }
+    }
+}
+
 // ------------------------------------------------------------------- Step B
+// Two bands of work items: J0 covers the first rows with large items, J1 the
+// last rows with small ones.  Blocks are issued in index order, so the small
+// items run last and fill the SMs that finish their large items early.
 template <int K, int VAR>
-__global__ void __launch_bounds__(256) k_stepB(StepBJob J, uint32_t nitems)
+__global__ void __launch_bounds__(256) k_stepB(StepBJob J0, uint32_t n0, StepBJob J1, uint32_t n1)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *sm = reinterpret_cast<WarpSmem *>(smem_raw);
     const uint32_t warp = threadIdx.x >> 5;
     const uint32_t item = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (item >= nitems) return;
-    stepb_item<K, VAR>(J, item, sm[warp]);
+    if (item < n0)
+        stepb_item<K, VAR>(J0, item, sm[warp]);
+    else if (item - n0 < n1)
+        stepb_item<K, VAR>(J1, item - n0, sm[warp]);
 }
 
 cudaError_t launch_powtab(const BetaArg &beta, uint32_t E, uint32_t dp1, const ModCtx &mc, uint64_t *ptab,
@@ -63,8 +96,25 @@ cudaError_t launch_stepA(const void *exps, uint32_t exp_bytes, uint64_t s, uint3
     return cudaGetLastError();
 }
 
+cudaError_t launch_stepA_starts(const void *exps, uint32_t exp_bytes, const uint64_t *coeffs, uint64_t s, uint32_t E,
+                               const uint64_t *ptab, uint32_t dp1, const ModCtx &mc, uint64_t t0, const StartRows &sr,
+                               uint64_t *mR, uint64_t *vstart, int num_sms, cudaStream_t st)
+{
+    if (s == 0) return cudaSuccess;
+    const uint64_t want = (s + 255) / 256;
+    const uint32_t grid = (uint32_t)(want < (uint64_t)num_sms * 16 ? want : (uint64_t)num_sms * 16);
+    if (exp_bytes == 1)
+        k_stepA_starts<uint8_t><<<grid, 256, 0, st>>>((const uint8_t *)exps, coeffs, s, E, ptab, dp1, mc, t0, sr,
+                                                      mR, vstart);
+    else
+        k_stepA_starts<uint16_t><<<grid, 256, 0, st>>>((const uint16_t *)exps, coeffs, s, E, ptab, dp1, mc, t0, sr,
+                                                       mR, vstart);
+    return cudaGetLastError();
+}
+
 template <int K, int VAR>
-static cudaError_t launch_b(const StepBJob &J, uint32_t nitems, int wpb, cudaStream_t st, int *occ)
+static cudaError_t launch_b(const StepBJob &J, uint32_t nitems, const StepBJob &J1, uint32_t n1, int wpb,
+                           cudaStream_t st, int *occ)
 {
     const size_t smem = (size_t)wpb * sizeof(WarpSmem);
     static bool attr_set = false;   // once, at the largest block (8 warps)
@@ -75,45 +125,48 @@ static cudaError_t launch_b(const StepBJob &J, uint32_t nitems, int wpb, cudaStr
         attr_set = true;
     }
     if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_stepB<K, VAR>, wpb * 32, smem);
-    if (nitems == 0) return cudaSuccess;
-    const uint32_t grid = (nitems + wpb - 1) / wpb;
-    k_stepB<K, VAR><<<grid, wpb * 32, smem, st>>>(J, nitems);
+    if (nitems + n1 == 0) return cudaSuccess;
+    const uint32_t grid = (nitems + n1 + wpb - 1) / wpb;
+    k_stepB<K, VAR><<<grid, wpb * 32, smem, st>>>(J, nitems, J1, n1);
     return cudaGetLastError();
 }
 
 template <int VAR>
-static cudaError_t dispatch_k(int K, const StepBJob &J, uint32_t nitems, int wpb, cudaStream_t st, int *occ)
+static cudaError_t dispatch_k(int K, const StepBJob &J, uint32_t n0, const StepBJob &J1, uint32_t n1, int wpb,
+                              cudaStream_t st, int *occ)
 {
     switch (K) {
-    case 1: return launch_b<1, VAR>(J, nitems, wpb, st, occ);
-    case 2: return launch_b<2, VAR>(J, nitems, wpb, st, occ);
-    case 4: return launch_b<4, VAR>(J, nitems, wpb, st, occ);
-    case 8: return launch_b<8, VAR>(J, nitems, wpb, st, occ);
-    case 16: return launch_b<16, VAR>(J, nitems, wpb, st, occ);
+    case 1: return launch_b<1, VAR>(J, n0, J1, n1, wpb, st, occ);
+    case 2: return launch_b<2, VAR>(J, n0, J1, n1, wpb, st, occ);
+    case 4: return launch_b<4, VAR>(J, n0, J1, n1, wpb, st, occ);
+    case 8: return launch_b<8, VAR>(J, n0, J1, n1, wpb, st, occ);
+    case 16: return launch_b<16, VAR>(J, n0, J1, n1, wpb, st, occ);
     default: return cudaErrorInvalidValue;
     }
 }
 
-static cudaError_t dispatch(int K, int var, const StepBJob &J, uint32_t nitems, int wpb, cudaStream_t st, int *occ)
+static cudaError_t dispatch(int K, int var, const StepBJob &J, uint32_t n0, const StepBJob &J1, uint32_t n1, int wpb,
+                            cudaStream_t st, int *occ)
 {
     if (wpb < 1 || wpb > 8) return cudaErrorInvalidValue;
     switch (var) {
-    case VAR_BARRETT: return dispatch_k<VAR_BARRETT>(K, J, nitems, wpb, st, occ);
-    case VAR_MONT: return dispatch_k<VAR_MONT>(K, J, nitems, wpb, st, occ);
-    case VAR_FP64: return dispatch_k<VAR_FP64>(K, J, nitems, wpb, st, occ);
+    case VAR_BARRETT: return dispatch_k<VAR_BARRETT>(K, J, n0, J1, n1, wpb, st, occ);
+    case VAR_MONT: return dispatch_k<VAR_MONT>(K, J, n0, J1, n1, wpb, st, occ);
+    case VAR_FP64: return dispatch_k<VAR_FP64>(K, J, n0, J1, n1, wpb, st, occ);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_stepB(int K, int var, const StepBJob &J, uint32_t nitems, int wpb, cudaStream_t st)
+cudaError_t launch_stepB(int K, int var, const StepBJob &J0, uint32_t n0, const StepBJob &J1, uint32_t n1, int wpb,
+                         cudaStream_t st)
 {
-    return dispatch(K, var, J, nitems, wpb, st, nullptr);
+    return dispatch(K, var, J0, n0, J1, n1, wpb, st, nullptr);
 }
 
 cudaError_t stepB_occupancy(int K, int var, int wpb, int *blocks_per_sm)
 {
     StepBJob dummy{};
-    return dispatch(K, var, dummy, 0, wpb, nullptr, blocks_per_sm);
+    return dispatch(K, var, dummy, 0, dummy, 0, wpb, nullptr, blocks_per_sm);
 }
 
 }  // namespace pe

@@ -164,16 +164,17 @@ __device__ __forceinline__ void stepb_item(const StepBJob &J, uint32_t item, War
             cnt = J.cs[c + 1] - start;
             gid = J.cg[c];
         }
-        // Jump start: v = a_i * m_i^(t0 + r_begin).
+        // Starting values a_i * m_i^(t0 + r_begin): precomputed by Step A for
+        // plain runs, otherwise by square-and-multiply here (jump start).
         const uint64_t e = J.t0 + r_begin;
         Lane<VAR> st[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if ((uint32_t)k < cnt) {
                 const uint64_t i = (uint64_t)start + k;
-                const uint64_t a = J.coeffs[i];
                 const uint64_t mR = J.mR ? J.mR[i] : fused_monomial(J, i);
-                const uint64_t v0 = canon(mont_mul(a, mont_pow(mR, e, mc), mc), mc.p);
+                const uint64_t v0 = J.vstart ? J.vstart[(uint64_t)(J.vs_base + q) * J.s + i]
+                                             : canon(mont_mul(J.coeffs[i], mont_pow(mR, e, mc), mc), mc.p);
                 st[k].init(v0, mR, mc);
             } else {
                 st[k].zero();

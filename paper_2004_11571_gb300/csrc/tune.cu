@@ -84,6 +84,7 @@ extern "C" pe_status poly_eval_tune(pe_poly *P, uint64_t T, pe_tiles *best, doub
                 P->forced = t;
                 P->requested_variant = v;
                 P->plan.valid = false;
+                P->tail_plan.valid = false;
                 pe_status s = poly_eval_run(P, beta.data(), T, 1, out.as<uint64_t>(), st);  // warm-up + plan
                 if (s != PE_OK) {
                     result = s;

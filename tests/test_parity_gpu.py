@@ -76,6 +76,32 @@ def test_automatic_tiles_and_ragged_sizes():
         _check_full(w)
 
 
+def test_tail_band_of_small_items():
+    # A forced band of one-slab items over the last points, issued after the others.
+    w = wl.make_zipf(n=7, s=400_000, p=P62, deg12=40, deg_rest=9, T=512, seed=19)
+    poly = pe.Poly.from_workload(w)
+    poly.set_tiles(K=8, slabs=2, tchunk=200, tail=100)
+    info = poly.plan_info(w.T)
+    assert info["tail_points"] > 0, info
+    got = pe.to_u64(poly.run(w.beta, w.T, 3))
+    cells = oracle.CellOracle(w)
+    rows = np.concatenate([np.arange(w.T - info["tail_points"] - 2, w.T), np.random.default_rng(1).integers(0, w.T, 30)])
+    cols = np.random.default_rng(2).integers(0, cells.G, rows.shape[0])
+    cols[:3] = 0
+    assert np.array_equal(got[rows, cols], cells(rows + 3, cols))
+    mont = pe.Poly.from_workload(w, variant="mont64")
+    assert np.array_equal(pe.to_u64(mont.run(w.beta, w.T, 3)), got)     # automatic tiles, no tail
+    poly.close()
+    mont.close()
+
+
+def test_many_t_chunks_fall_back_to_jump_start():
+    # More T-chunks than precomputed start rows: items start by square-and-multiply.
+    w = wl.make_zipf(n=6, s=3_000, p=P62, deg12=6, deg_rest=5, T=4_200, seed=20)
+    _check_full(w, "barrett64", dict(K=4, slabs=1, tchunk=32), t0=5)
+    _check_full(w, "barrett64", dict(K=8, slabs=2, tchunk=256), t0=5)
+
+
 @pytest.mark.parametrize("t0", [0, 1, 7, 123_456, 1 << 40])
 def test_start_points(t0):
     w = wl.make_uniform(n=5, s=5_000, p=P62, deg12=6, deg_rest=7, T=70, seed=9)
