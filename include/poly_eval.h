@@ -270,11 +270,12 @@ typedef struct {
 typedef struct pe_server pe_server;
 
 /*
- * One request.  Exactly one of `poly_desc` (a new polynomial, uploaded by the
- * server) and `resident_id` (a polynomial registered with
- * poly_eval_server_register, reused at a new beta) is used: resident_id = 0
- * selects poly_desc.  `out` is a host buffer of T x G uint64 that must stay
- * valid until the ticket completes.
+ * One request.  Exactly one of `poly_desc` (a new polynomial, copied at
+ * submit and uploaded by the server) and `resident_id` (a polynomial already
+ * on the device, reused at a new beta) is used: resident_id = 0 selects
+ * poly_desc.  `out` is a host buffer of T x G uint64 that must stay valid
+ * until the ticket completes; page-locked buffers are filled by an
+ * asynchronous copy, others through a staging buffer.
  */
 typedef struct {
     const pe_poly_desc *poly_desc;
@@ -283,6 +284,9 @@ typedef struct {
     uint64_t T;
     uint64_t t0;
     uint64_t *out;
+    uint64_t *new_resident_id; /* optional: with poly_desc, receives the id under which the uploaded
+                                  polynomial stays resident for later requests (evicted least
+                                  recently used first when memory is needed) */
 } pe_request;
 
 typedef struct {

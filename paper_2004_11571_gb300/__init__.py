@@ -72,7 +72,8 @@ class _ServerCfg(ctypes.Structure):
 
 class _Request(ctypes.Structure):
     _fields_ = [("poly_desc", ctypes.c_void_p), ("resident_id", ctypes.c_uint64), ("beta", ctypes.c_void_p),
-                ("T", ctypes.c_uint64), ("t0", ctypes.c_uint64), ("out", ctypes.c_void_p)]
+                ("T", ctypes.c_uint64), ("t0", ctypes.c_uint64), ("out", ctypes.c_void_p),
+                ("new_resident_id", ctypes.c_void_p)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -306,6 +307,71 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib().poly_eval_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server (poly_eval_server_*).
+
+    submit() returns a ticket; results land in the caller's host buffer `out`
+    (T x G uint64; page-locked buffers take the asynchronous path)."""
+
+    def __init__(self, mem_cap_bytes: int = 40 << 30, max_queue: int = 4096, max_epoch_jobs: int = 256,
+                 streams: int = 2):
+        cfg = _ServerCfg(int(mem_cap_bytes), int(max_queue), int(max_epoch_jobs), int(streams))
+        h = ctypes.c_void_p()
+        _check(lib().poly_eval_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def register(self, p: int, coeffs, exps, variant="auto") -> int:
+        desc, keep = _make_desc(int(p), coeffs, exps, variant, False)
+        rid = ctypes.c_uint64()
+        _check(lib().poly_eval_server_register(self._h, ctypes.byref(desc), ctypes.byref(rid)))
+        return int(rid.value)
+
+    def submit(self, beta, T: int, out: np.ndarray, t0: int = 1, poly=None, resident_id: int = 0,
+               variant="auto"):
+        """poly = (p, coeffs, exps) uploads a new polynomial; returns (ticket, new_resident_id)."""
+        b = np.ascontiguousarray(np.asarray(beta, dtype=np.uint64).reshape(-1))
+        new_id = ctypes.c_uint64(0)
+        desc_ref = None
+        keep = None
+        if poly is not None:
+            desc, keep = _make_desc(int(poly[0]), poly[1], poly[2], variant, False)
+            desc_ref = ctypes.addressof(desc)
+        req = _Request(desc_ref, int(resident_id), b.ctypes.data if b.size else None, int(T), int(t0),
+                       out.ctypes.data, ctypes.addressof(new_id))
+        t = ctypes.c_uint64()
+        _check(lib().poly_eval_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        del keep, desc_ref
+        self._keep[int(t.value)] = out
+        return int(t.value), int(new_id.value)
+
+    def poll(self, ticket: int, timeout_us: int = -1) -> int:
+        """Status code: 0 done, 9 pending (timeout 0), 8 timed out; errors raise."""
+        st = lib().poly_eval_server_poll(self._h, int(ticket), int(timeout_us))
+        if st in (PE_OK, PE_PENDING, PE_ERR_TIMEOUT):
+            if st == PE_OK:
+                self._keep.pop(int(ticket), None)
+            return st
+        self._keep.pop(int(ticket), None)
+        _check(st)
+
+    def stats(self) -> dict:
+        s = _ServerStats()
+        _check(lib().poly_eval_server_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().poly_eval_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -155,33 +155,6 @@ static Tiles batch_tiles(pe_poly *P, uint64_t T, double w_target)
 
 static int resolve_variant(pe_poly *P, uint64_t T) { return run_variant(P, T); }
 
-}  // namespace pe
-
-using namespace pe;
-
-struct pe_batch {
-    std::vector<pe_job> jobs;
-    std::vector<std::vector<uint64_t>> betas;
-    std::vector<size_t> beta_off;      // arena offset of each job's beta
-    DevBuf arena;
-    size_t counters_off = 0, counters_bytes = 0;
-    StepBJob *d_jobs = nullptr;
-    uint2 *d_items = nullptr;
-    PowJob *d_pow = nullptr;
-    uint32_t *d_head = nullptr;
-    uint32_t nitems = 0, njobs_live = 0, max_entries = 0;
-    cudaStream_t cap = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int grid = 0;
-    ~pe_batch()
-    {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        if (cap) cudaStreamDestroy(cap);
-    }
-};
-
 namespace {
 
 struct Layout {
@@ -196,41 +169,32 @@ struct Layout {
 
 }  // namespace
 
-extern "C" pe_status poly_eval_batch_plan(const pe_job *jobs, size_t njobs, pe_batch **out)
+// Plans every job, lays the plans, power tables, scratch and the ordered work
+// queue out in `arena` (grown only when too small) and fills `img.host` with
+// the bytes to upload there.
+pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImage &img)
 {
-    if (!out) {
-        set_error("out is NULL");
-        return PE_ERR_ARG;
-    }
-    *out = nullptr;
+    img = BatchImage{};
     if (njobs && !jobs) {
         set_error("jobs is NULL");
         return PE_ERR_ARG;
     }
-    pe_batch *B = new pe_batch();
-    B->jobs.assign(jobs, jobs + njobs);
-    B->betas.resize(njobs);
-    // Validation and work totals.
+    img.betas.resize(njobs);
     double w_total = 0.0;
     for (size_t j = 0; j < njobs; ++j) {
         const pe_job &jb = jobs[j];
         if (!jb.poly || (jb.T && jb.poly->G && !jb.out) || jb.T > (1ull << 31)) {
             set_error("job %zu: NULL poly/out or T above 2^31", j);
-            delete B;
             return PE_ERR_ARG;
         }
         BetaArg ba;
         pe_status st = check_beta(jb.poly, jb.beta, &ba);
-        if (st != PE_OK) {
-            delete B;
-            return st;
-        }
-        B->betas[j].assign(ba.b, ba.b + jb.poly->E);
+        if (st != PE_OK) return st;
+        img.betas[j].assign(ba.b, ba.b + jb.poly->E);
         w_total += (double)jb.poly->s * (double)jb.T;
     }
     const uint64_t R = queue_resident_warps();
     const double w_target = std::max(w_total / (8.0 * (double)R), 32.0 * 64.0);
-    // Per-job plans and arena layout.
     std::vector<PlanHost> ph(njobs);
     std::vector<std::vector<uint32_t>> cs(njobs), cg(njobs);
     std::vector<int> var(njobs);
@@ -239,7 +203,7 @@ extern "C" pe_status poly_eval_batch_plan(const pe_job *jobs, size_t njobs, pe_b
     const size_t off_pow = L.take(std::max<size_t>(njobs, 1) * sizeof(PowJob));
     std::vector<size_t> o_cs(njobs), o_cg(njobs), o_unit(njobs), o_span(njobs), o_carry(njobs), o_chain(njobs),
         o_ptab(njobs), o_cnt(njobs);
-    B->beta_off.resize(njobs);
+    img.beta_off.assign(njobs, 0);
     for (size_t j = 0; j < njobs; ++j) {
         pe_poly *P = jobs[j].poly;
         if (!jobs[j].T || !P->G) continue;
@@ -255,14 +219,14 @@ extern "C" pe_status poly_eval_batch_plan(const pe_job *jobs, size_t njobs, pe_b
         o_carry[j] = L.take(ph[j].carry_bytes());
         o_chain[j] = L.take(ph[j].chain_bytes());
         o_ptab[j] = L.take((size_t)std::max<uint32_t>(P->E, 1) * (P->dmax + 1) * 8);
-        B->beta_off[j] = L.take((size_t)std::max<uint32_t>(P->E, 1) * 8);
+        img.beta_off[j] = L.take((size_t)std::max<uint32_t>(P->E, 1) * 8);
     }
-    // Counters (and the queue head) in one contiguous region, cleared by the graph.
-    B->counters_off = L.off;
+    // Counters (and the queue head) in one contiguous region, cleared before each launch.
+    img.counters_off = L.off;
     const size_t off_head = L.take(256);
     for (size_t j = 0; j < njobs; ++j)
         if (jobs[j].T && jobs[j].poly->G) o_cnt[j] = L.take(ph[j].counter_bytes());
-    B->counters_bytes = L.off - B->counters_off;
+    img.counters_bytes = L.off - img.counters_off;
     // Items, ordered by decreasing cost (a slab-point of a K-term chunk costs K).
     std::vector<std::pair<double, uint2>> items;
     for (size_t j = 0; j < njobs; ++j) {
@@ -281,15 +245,12 @@ extern "C" pe_status poly_eval_batch_plan(const pe_job *jobs, size_t njobs, pe_b
     }
     std::stable_sort(items.begin(), items.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
     const size_t off_items = L.take(std::max<size_t>(items.size(), 1) * sizeof(uint2));
-    cudaError_t e = B->arena.ensure(L.off);
-    if (e != cudaSuccess) {
-        delete B;
-        return cuda_fail(e, "batch arena");
-    }
-    unsigned char *base = B->arena.as<unsigned char>();
-    std::vector<unsigned char> host(L.off, 0);
+    cudaError_t e = arena.ensure(L.off);
+    if (e != cudaSuccess) return cuda_fail(e, "batch arena");
+    unsigned char *base = arena.as<unsigned char>();
+    img.host.assign(L.off, 0);
     auto put = [&](size_t off, const void *src, size_t n) {
-        if (n) memcpy(host.data() + off, src, n);
+        if (n) memcpy(img.host.data() + off, src, n);
     };
     std::vector<StepBJob> hj(njobs);
     std::vector<PowJob> hp(njobs);
@@ -301,52 +262,103 @@ extern "C" pe_status poly_eval_batch_plan(const pe_job *jobs, size_t njobs, pe_b
         put(o_cg[j], cg[j].data(), cg[j].size() * 4);
         put(o_unit[j], ph[j].unit.data(), ph[j].unit.size() * 4);
         put(o_span[j], ph[j].span.data(), ph[j].span.size() * 4);
-        put(B->beta_off[j], B->betas[j].data(), B->betas[j].size() * 8);
+        put(img.beta_off[j], img.betas[j].data(), img.betas[j].size() * 8);
         fill_job(hj[j], P, ph[j], (const uint32_t *)(base + o_cs[j]), (const uint32_t *)(base + o_cg[j]),
                  (const int32_t *)(base + o_unit[j]), (const uint32_t *)(base + o_span[j]),
                  (uint32_t *)(base + o_cnt[j]), (ulonglong2 *)(base + o_carry[j]), (ulonglong2 *)(base + o_chain[j]),
                  jb.t0, jb.out, nullptr, (const uint64_t *)(base + o_ptab[j]), var[j]);
-        hp[j].beta = (const uint64_t *)(base + B->beta_off[j]);
+        hp[j].beta = (const uint64_t *)(base + img.beta_off[j]);
         hp[j].ptab = (uint64_t *)(base + o_ptab[j]);
         hp[j].E = P->E;
         hp[j].dp1 = P->dmax + 1;
         hp[j].mc = P->mc;
-        B->max_entries = std::max(B->max_entries, P->E * (P->dmax + 1));
+        img.max_entries = std::max(img.max_entries, P->E * (P->dmax + 1));
     }
     put(off_jobs, hj.data(), njobs * sizeof(StepBJob));
     put(off_pow, hp.data(), njobs * sizeof(PowJob));
     std::vector<uint2> it(items.size());
     for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
     put(off_items, it.data(), it.size() * sizeof(uint2));
-    if ((e = cudaMemcpy(base, host.data(), L.off, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    img.base = base;
+    img.d_jobs = (StepBJob *)(base + off_jobs);
+    img.d_pow = (PowJob *)(base + off_pow);
+    img.d_items = (uint2 *)(base + off_items);
+    img.d_head = (uint32_t *)(base + off_head);
+    img.nitems = (uint32_t)items.size();
+    img.njobs = (uint32_t)njobs;
+    int bps = 0;
+    if ((e = queue_setup(&bps)) != cudaSuccess) return cuda_fail(e, "queue kernel setup");
+    img.grid = std::max(1, bps) * num_sms();
+    img.term_points = w_total;
+    return PE_OK;
+}
+
+// Clears the counters, builds every job's power tables and runs the queue.
+cudaError_t batch_kernels(const BatchImage &img, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(img.base + img.counters_off, 0, img.counters_bytes, st);
+    if (e != cudaSuccess) return e;
+    if (img.max_entries && img.njobs)
+        k_powtab_batch<<<dim3((img.max_entries + 127) / 128, img.njobs), 128, 0, st>>>(img.d_pow);
+    if (img.nitems)
+        k_stepB_queue<<<img.grid, kQueueWarps * 32, queue_smem(), st>>>(img.d_jobs, img.d_items, img.nitems,
+                                                                        img.d_head);
+    return cudaGetLastError();
+}
+
+// Uploads the image (stream-ordered) and runs it.
+cudaError_t batch_enqueue(const BatchImage &img, cudaStream_t st)
+{
+    cudaError_t e = cudaMemcpyAsync(img.base, img.host.data(), img.host.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return batch_kernels(img, st);
+}
+
+}  // namespace pe
+
+using namespace pe;
+
+struct pe_batch {
+    std::vector<pe_job> jobs;
+    BatchImage img;
+    DevBuf arena;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~pe_batch()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+extern "C" pe_status poly_eval_batch_plan(const pe_job *jobs, size_t njobs, pe_batch **out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return PE_ERR_ARG;
+    }
+    *out = nullptr;
+    pe_batch *B = new pe_batch();
+    if (njobs && jobs) B->jobs.assign(jobs, jobs + njobs);
+    pe_status st = batch_build(jobs, njobs, B->arena, B->img);
+    if (st != PE_OK) {
+        delete B;
+        return st;
+    }
+    cudaError_t e = cudaMemcpy(B->img.base, B->img.host.data(), B->img.host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
         delete B;
         return cuda_fail(e, "batch upload");
     }
-    B->d_jobs = (StepBJob *)(base + off_jobs);
-    B->d_pow = (PowJob *)(base + off_pow);
-    B->d_items = (uint2 *)(base + off_items);
-    B->d_head = (uint32_t *)(base + off_head);
-    B->nitems = (uint32_t)items.size();
-    B->njobs_live = (uint32_t)njobs;
-    int bps = 0;
-    if ((e = queue_setup(&bps)) != cudaSuccess) {
-        delete B;
-        return cuda_fail(e, "queue kernel setup");
-    }
-    B->grid = std::max(1, bps) * num_sms();
     // Capture the batch as a CUDA graph on a private stream.
     if ((e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
         delete B;
         return cuda_fail(e, "graph capture");
     }
-    cudaMemsetAsync(base + B->counters_off, 0, B->counters_bytes, B->cap);
-    if (B->max_entries && njobs)
-        k_powtab_batch<<<dim3((B->max_entries + 127) / 128, (unsigned)njobs), 128, 0, B->cap>>>(B->d_pow);
-    if (B->nitems)
-        k_stepB_queue<<<B->grid, kQueueWarps * 32, queue_smem(), B->cap>>>(B->d_jobs, B->d_items, B->nitems,
-                                                                           B->d_head);
-    cudaError_t le = cudaGetLastError();
+    cudaError_t le = batch_kernels(B->img, B->cap);
     e = cudaStreamEndCapture(B->cap, &B->graph);
     if (le != cudaSuccess) e = le;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
@@ -380,8 +392,8 @@ extern "C" pe_status poly_eval_batch_set_beta(pe_batch *B, size_t j, const uint6
     if (st != PE_OK) return st;
     const uint32_t E = B->jobs[j].poly->E;
     if (!E) return PE_OK;
-    B->betas[j].assign(ba.b, ba.b + E);
-    cudaError_t e = cudaMemcpy(B->arena.as<unsigned char>() + B->beta_off[j], B->betas[j].data(), E * 8,
+    B->img.betas[j].assign(ba.b, ba.b + E);
+    cudaError_t e = cudaMemcpy(B->img.base + B->img.beta_off[j], B->img.betas[j].data(), E * 8,
                                cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "beta upload");
     return PE_OK;

@@ -79,6 +79,27 @@ struct Tiles {
     uint32_t tailT = 0;   // points in the tail band of one-slab items (0: none)
 };
 
+struct PowJob;
+
+// A planned batch laid out in a device arena (see batch.cu).
+struct BatchImage {
+    std::vector<unsigned char> host;          // bytes to upload at `base`
+    std::vector<std::vector<uint64_t>> betas;
+    std::vector<size_t> beta_off;
+    unsigned char *base = nullptr;
+    size_t counters_off = 0, counters_bytes = 0;
+    StepBJob *d_jobs = nullptr;
+    PowJob *d_pow = nullptr;
+    uint2 *d_items = nullptr;
+    uint32_t *d_head = nullptr;
+    uint32_t nitems = 0, njobs = 0, max_entries = 0;
+    int grid = 0;
+    double term_points = 0.0;
+};
+
+pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImage &img);
+cudaError_t batch_enqueue(const BatchImage &img, cudaStream_t st);
+
 }  // namespace pe
 
 struct pe_poly {

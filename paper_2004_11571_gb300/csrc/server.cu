@@ -1,0 +1,534 @@
+// Server: continuous batching of evaluation requests.
+//
+// Clients submit requests (a polynomial to upload, or one already resident,
+// with beta, T, t0 and a host output buffer) into a bounded backlog.  A worker
+// thread forms an epoch whenever one of its streams is free: it admits
+// backlog requests in arrival order while their device memory fits under the
+// cap (evicting resident polynomials least recently used first), uploads new
+// polynomials, plans the epoch as one batch (persistent queue kernel, see
+// batch.cu) into that stream's reusable arena and launches it.  Epochs on
+// different streams overlap on the GPU, so requests that arrive while others
+// run are admitted as soon as a stream and memory are free.  Results go back
+// with an asynchronous copy (page-locked outputs) or through a staging buffer.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+#include "internal.h"
+
+namespace pe {
+
+using Clock = std::chrono::steady_clock;
+
+struct SrvRequest {
+    uint64_t ticket = 0;
+    uint64_t resident_id = 0;         // 0: upload `desc`
+    pe_poly_desc desc{};
+    std::vector<uint64_t> coeffs;
+    std::vector<uint8_t> exps;
+    std::vector<uint64_t> beta;
+    uint64_t T = 0, t0 = 0;
+    uint64_t *out = nullptr;
+    bool out_pinned = false;
+    uint64_t *new_id_out = nullptr;
+    Clock::time_point submitted;
+    pe_poly *poly = nullptr;          // once admitted
+    uint64_t used_id = 0;
+    size_t out_off = 0, out_bytes = 0;
+    uint64_t g_est = 0;               // bound on the group count of an upload
+};
+
+struct Resident {
+    pe_poly *poly = nullptr;
+    uint64_t bytes = 0;
+    uint64_t last_use = 0;
+    uint32_t refs = 0;                // admitted requests using it
+    bool pinned = false;              // registered by the client: never evicted
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    DevBuf arena, outs;
+    void *staging = nullptr;          // page-locked bounce buffer for pageable outputs
+    size_t staging_bytes = 0;
+    BatchImage img;
+    std::vector<SrvRequest *> reqs;
+    bool busy = false;
+    double term_points = 0.0;
+};
+
+static uint64_t poly_bytes_estimate(const pe_poly_desc &d)
+{
+    const uint64_t E = d.n >= 2 ? d.n - 2 : 0;
+    return d.s * (8 + 8 + E * 2) + 4096;
+}
+
+}  // namespace pe
+
+using namespace pe;
+
+struct pe_server {
+    pe_server_cfg cfg{};
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<SrvRequest *> backlog;
+    std::unordered_map<uint64_t, int> status;   // ticket -> PE_PENDING / PE_OK / error
+    std::unordered_map<uint64_t, Resident> store;
+    uint64_t next_ticket = 1, next_id = 1, use_clock = 0;
+    uint64_t resident_bytes = 0;
+    Slot slots[4];
+    uint32_t nslots = 0;
+    std::thread worker;
+    bool stop = false;
+    // statistics
+    uint64_t submitted = 0, completed = 0, rejected = 0, epochs = 0, evictions = 0;
+    std::vector<double> lat_ms;
+    double term_points = 0.0, busy_s = 0.0;
+    Clock::time_point busy_since;
+    int inflight = 0;
+
+    uint64_t committed() const
+    {
+        uint64_t b = resident_bytes;
+        for (uint32_t i = 0; i < nslots; ++i) b += slots[i].arena.bytes + slots[i].outs.bytes;
+        return b;
+    }
+
+    // Evicts unreferenced, unpinned residents (least recently used first) until
+    // `need` more bytes fit under the cap.  Called with `mu` held.
+    bool make_room(uint64_t need)
+    {
+        while (committed() + need > cfg.mem_cap_bytes) {
+            uint64_t victim = 0, oldest = ~0ull;
+            for (auto &kv : store)
+                if (!kv.second.pinned && kv.second.refs == 0 && kv.second.last_use < oldest) {
+                    oldest = kv.second.last_use;
+                    victim = kv.first;
+                }
+            if (!victim) return false;
+            Resident r = store[victim];
+            store.erase(victim);
+            resident_bytes -= r.bytes;
+            poly_eval_destroy(r.poly);
+            ++evictions;
+        }
+        return true;
+    }
+
+    void finish(Slot &s)
+    {
+        const Clock::time_point now = Clock::now();
+        for (SrvRequest *r : s.reqs) {
+            if (!r->out_pinned && r->out_bytes)
+                memcpy(r->out, (unsigned char *)s.staging + r->out_off, r->out_bytes);
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        for (SrvRequest *r : s.reqs) {
+            auto it = store.find(r->used_id);
+            if (it != store.end() && it->second.refs) it->second.refs--;
+            status[r->ticket] = PE_OK;
+            lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->submitted).count());
+            ++completed;
+            delete r;
+        }
+        term_points += s.term_points;
+        s.reqs.clear();
+        s.busy = false;
+        if (--inflight == 0) busy_s += std::chrono::duration<double>(now - busy_since).count();
+        cv_done.notify_all();
+    }
+
+    void fail(std::vector<SrvRequest *> &reqs, int code)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (SrvRequest *r : reqs) {
+            auto it = store.find(r->used_id);
+            if (it != store.end() && it->second.refs) it->second.refs--;
+            status[r->ticket] = code;
+            delete r;
+        }
+        reqs.clear();
+        cv_done.notify_all();
+    }
+
+    // Admits backlog requests into slot `s` and launches them as one epoch.
+    bool launch(Slot &s)
+    {
+        std::vector<SrvRequest *> take;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            uint64_t need = 0;
+            while (!backlog.empty() && take.size() < cfg.max_epoch_jobs) {
+                SrvRequest *r = backlog.front();
+                uint64_t add = 0;
+                if (r->resident_id) {
+                    auto it = store.find(r->resident_id);
+                    if (it == store.end()) {
+                        status[r->ticket] = PE_ERR_NOT_FOUND;
+                        backlog.pop_front();
+                        delete r;
+                        cv_done.notify_all();
+                        continue;
+                    }
+                    r->poly = it->second.poly;
+                    add = r->T * r->poly->G * 8 + r->poly->s * 24 + r->T * 1024;
+                } else {
+                    add = poly_bytes_estimate(r->desc) + r->T * r->g_est * 8 + r->desc.s * 24 + r->T * 1024;
+                }
+                if (!make_room(need + add)) {
+                    if (take.empty() && inflight == 0) {   // can never fit
+                        status[r->ticket] = PE_ERR_ADMISSION;
+                        ++rejected;
+                        backlog.pop_front();
+                        delete r;
+                        cv_done.notify_all();
+                        continue;
+                    }
+                    break;
+                }
+                need += add;
+                backlog.pop_front();
+                if (r->resident_id) {
+                    Resident &res = store[r->resident_id];
+                    res.refs++;
+                    res.last_use = ++use_clock;
+                    r->used_id = r->resident_id;
+                }
+                take.push_back(r);
+            }
+        }
+        if (take.empty()) return false;
+        // Upload new polynomials (outside the lock).
+        std::vector<SrvRequest *> ok;
+        for (SrvRequest *r : take) {
+            if (!r->resident_id) {
+                r->desc.coeffs = r->coeffs.data();
+                r->desc.exps = r->exps.data();
+                pe_poly *P = nullptr;
+                const pe_status st = poly_eval_create(&r->desc, &P);
+                std::vector<uint8_t>().swap(r->exps);
+                std::vector<uint64_t>().swap(r->coeffs);
+                if (st != PE_OK) {
+                    std::vector<SrvRequest *> one{r};
+                    fail(one, st);
+                    continue;
+                }
+                std::lock_guard<std::mutex> lk(mu);
+                const uint64_t id = next_id++;
+                Resident res;
+                res.poly = P;
+                res.bytes = P->device_bytes();
+                res.refs = 1;
+                res.last_use = ++use_clock;
+                store[id] = res;
+                resident_bytes += res.bytes;
+                r->poly = P;
+                r->used_id = id;
+                if (r->new_id_out) *r->new_id_out = id;
+            }
+            ok.push_back(r);
+        }
+        if (ok.empty()) return false;
+        // Outputs, then the batch.
+        size_t total = 0;
+        for (SrvRequest *r : ok) {
+            r->out_bytes = r->T * r->poly->G * 8;
+            r->out_off = total;
+            total += (r->out_bytes + 255) / 256 * 256;
+        }
+        cudaError_t e = s.outs.ensure(std::max<size_t>(total, 256));
+        bool need_staging = false;
+        for (SrvRequest *r : ok) need_staging |= !r->out_pinned && r->out_bytes;
+        if (e == cudaSuccess && need_staging && s.staging_bytes < total) {
+            if (s.staging) cudaFreeHost(s.staging);
+            s.staging = nullptr;
+            s.staging_bytes = 0;
+            e = cudaMallocHost(&s.staging, total);
+            if (e == cudaSuccess) s.staging_bytes = total;
+        }
+        if (e != cudaSuccess) {
+            cuda_fail(e, "server outputs");
+            fail(ok, PE_ERR_NOMEM);
+            return true;
+        }
+        std::vector<pe_job> jobs(ok.size());
+        s.term_points = 0.0;
+        for (size_t j = 0; j < ok.size(); ++j) {
+            SrvRequest *r = ok[j];
+            jobs[j].poly = r->poly;
+            jobs[j].beta = r->beta.data();
+            jobs[j].T = r->T;
+            jobs[j].t0 = r->t0;
+            jobs[j].out = (uint64_t *)(s.outs.as<unsigned char>() + r->out_off);
+            s.term_points += (double)r->poly->s * (double)r->T;
+        }
+        pe_status st = batch_build(jobs.data(), jobs.size(), s.arena, s.img);
+        if (st == PE_OK && (e = batch_enqueue(s.img, s.st)) != cudaSuccess) st = cuda_fail(e, "server epoch");
+        for (size_t j = 0; st == PE_OK && j < ok.size(); ++j) {
+            SrvRequest *r = ok[j];
+            if (!r->out_bytes) continue;
+            void *dst = r->out_pinned ? (void *)r->out : (void *)((unsigned char *)s.staging + r->out_off);
+            if ((e = cudaMemcpyAsync(dst, jobs[j].out, r->out_bytes, cudaMemcpyDeviceToHost, s.st)) != cudaSuccess)
+                st = cuda_fail(e, "server copy back");
+        }
+        if (st == PE_OK && (e = cudaEventRecord(s.done, s.st)) != cudaSuccess) st = cuda_fail(e, "server event");
+        if (st != PE_OK) {
+            cudaStreamSynchronize(s.st);
+            fail(ok, st);
+            return true;
+        }
+        s.reqs = ok;
+        s.busy = true;
+        std::lock_guard<std::mutex> lk(mu);
+        if (inflight++ == 0) busy_since = Clock::now();
+        ++epochs;
+        return true;
+    }
+
+    void run()
+    {
+        cudaSetDevice(device);
+        for (;;) {
+            bool progressed = false;
+            for (uint32_t i = 0; i < nslots; ++i) {
+                Slot &s = slots[i];
+                if (s.busy && cudaEventQuery(s.done) == cudaSuccess) {
+                    finish(s);
+                    progressed = true;
+                } else if (s.busy) {
+                    cudaGetLastError();   // clear cudaErrorNotReady
+                }
+            }
+            for (uint32_t i = 0; i < nslots; ++i)
+                if (!slots[i].busy && launch(slots[i])) progressed = true;
+            std::unique_lock<std::mutex> lk(mu);
+            bool any_busy = false;
+            for (uint32_t i = 0; i < nslots; ++i) any_busy |= slots[i].busy;
+            if (stop && backlog.empty() && !any_busy) return;
+            if (!progressed) {
+                if (any_busy) {
+                    lk.unlock();
+                    std::this_thread::sleep_for(std::chrono::microseconds(20));
+                } else {
+                    cv_work.wait_for(lk, std::chrono::milliseconds(2));
+                }
+            }
+        }
+    }
+};
+
+extern "C" pe_status poly_eval_server_create(const pe_server_cfg *cfg, pe_server **out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return PE_ERR_ARG;
+    }
+    *out = nullptr;
+    pe_server *S = new pe_server();
+    pe_server_cfg c{};
+    if (cfg) c = *cfg;
+    if (!c.mem_cap_bytes) c.mem_cap_bytes = 40ull << 30;
+    if (!c.max_queue) c.max_queue = 4096;
+    if (!c.max_epoch_jobs) c.max_epoch_jobs = 256;
+    if (!c.streams) c.streams = 2;
+    c.streams = std::min<uint32_t>(c.streams, 4);
+    S->cfg = c;
+    cudaGetDevice(&S->device);
+    S->nslots = c.streams;
+    for (uint32_t i = 0; i < S->nslots; ++i) {
+        Slot &s = S->slots[i];
+        cudaError_t e;
+        if ((e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess) {
+            delete S;
+            return cuda_fail(e, "server streams");
+        }
+    }
+    S->worker = std::thread([S] { S->run(); });
+    *out = S;
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_server_register(pe_server *S, const pe_poly_desc *desc, uint64_t *resident_id)
+{
+    if (!S || !desc || !resident_id) {
+        set_error("NULL argument");
+        return PE_ERR_ARG;
+    }
+    pe_poly *P = nullptr;
+    pe_status st = poly_eval_create(desc, &P);
+    if (st != PE_OK) return st;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->make_room(P->device_bytes())) {
+        poly_eval_destroy(P);
+        set_error("resident store is full");
+        return PE_ERR_ADMISSION;
+    }
+    Resident r;
+    r.poly = P;
+    r.bytes = P->device_bytes();
+    r.pinned = true;
+    r.last_use = ++S->use_clock;
+    const uint64_t id = S->next_id++;
+    S->store[id] = r;
+    S->resident_bytes += r.bytes;
+    *resident_id = id;
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_server_submit(pe_server *S, const pe_request *req, uint64_t *ticket)
+{
+    if (!S || !req || !ticket || !req->out || (!req->resident_id && !req->poly_desc)) {
+        set_error("bad request");
+        return PE_ERR_ARG;
+    }
+    if (req->T > (1ull << 31)) {
+        set_error("T above 2^31");
+        return PE_ERR_ARG;
+    }
+    SrvRequest *r = new SrvRequest();
+    r->resident_id = req->resident_id;
+    r->T = req->T;
+    r->t0 = req->t0;
+    r->out = req->out;
+    r->new_id_out = req->new_resident_id;
+    cudaPointerAttributes a{};
+    r->out_pinned = cudaPointerGetAttributes(&a, req->out) == cudaSuccess && a.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    uint32_t n = 0;
+    if (!req->resident_id) {
+        const pe_poly_desc &d = *req->poly_desc;
+        if ((d.flags & PE_FLAG_DEVICE_PTRS) || (d.s && (!d.coeffs || !d.exps)) ||
+            (d.exp_bytes != 1 && d.exp_bytes != 2 && d.exp_bytes != 4) || d.n < 2 || d.n > PE_MAX_VARS) {
+            delete r;
+            set_error("poly_desc must describe host arrays");
+            return PE_ERR_ARG;
+        }
+        r->desc = d;
+        r->coeffs.assign(d.coeffs, d.coeffs + d.s);
+        const uint8_t *e = (const uint8_t *)d.exps;
+        r->exps.assign(e, e + d.s * d.n * d.exp_bytes);
+        n = d.n;
+        uint64_t md = 0, me = 0;   // the groups lie in a (max d + 1) x (max e + 1) grid
+        for (uint64_t i = 0; i < d.s; ++i) {
+            uint64_t x0, x1;
+            if (d.exp_bytes == 1) x0 = e[i * d.n], x1 = e[i * d.n + 1];
+            else if (d.exp_bytes == 2) x0 = ((const uint16_t *)e)[i * d.n], x1 = ((const uint16_t *)e)[i * d.n + 1];
+            else x0 = ((const uint32_t *)e)[i * d.n], x1 = ((const uint32_t *)e)[i * d.n + 1];
+            md = std::max(md, x0);
+            me = std::max(me, x1);
+        }
+        r->g_est = std::min<uint64_t>(d.s, (md + 1) * (me + 1));
+    } else {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->store.find(req->resident_id);
+        if (it == S->store.end()) {
+            delete r;
+            set_error("unknown resident id");
+            return PE_ERR_NOT_FOUND;
+        }
+        n = it->second.poly->n;
+    }
+    if (n > 2) {
+        if (!req->beta) {
+            delete r;
+            set_error("beta is NULL");
+            return PE_ERR_ARG;
+        }
+        r->beta.assign(req->beta, req->beta + (n - 2));
+    }
+    r->submitted = Clock::now();
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->backlog.size() >= S->cfg.max_queue) {
+        ++S->rejected;
+        delete r;
+        set_error("backlog full");
+        return PE_ERR_ADMISSION;
+    }
+    r->ticket = S->next_ticket++;
+    S->status[r->ticket] = PE_PENDING;
+    S->backlog.push_back(r);
+    ++S->submitted;
+    *ticket = r->ticket;
+    S->cv_work.notify_one();
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_server_poll(pe_server *S, uint64_t ticket, int64_t timeout_us)
+{
+    if (!S) {
+        set_error("NULL server");
+        return PE_ERR_ARG;
+    }
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto done = [&] {
+        auto it = S->status.find(ticket);
+        return it == S->status.end() || it->second != PE_PENDING;
+    };
+    if (timeout_us < 0) S->cv_done.wait(lk, done);
+    else if (timeout_us > 0) S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), done);
+    auto it = S->status.find(ticket);
+    if (it == S->status.end()) {
+        set_error("unknown ticket");
+        return PE_ERR_NOT_FOUND;
+    }
+    const int st = it->second;
+    if (st == PE_PENDING) return timeout_us == 0 ? PE_PENDING : PE_ERR_TIMEOUT;
+    S->status.erase(it);
+    return (pe_status)st;
+}
+
+extern "C" pe_status poly_eval_server_stats(pe_server *S, pe_server_stats *out)
+{
+    if (!S || !out) {
+        set_error("NULL argument");
+        return PE_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    memset(out, 0, sizeof *out);
+    out->submitted = S->submitted;
+    out->completed = S->completed;
+    out->rejected = S->rejected;
+    out->epochs = S->epochs;
+    out->term_points = S->term_points;
+    out->busy_s = S->busy_s + (S->inflight ? std::chrono::duration<double>(Clock::now() - S->busy_since).count() : 0);
+    out->resident_bytes = S->resident_bytes;
+    out->resident_polys = S->store.size();
+    out->evictions = S->evictions;
+    if (!S->lat_ms.empty()) {
+        std::vector<double> v = S->lat_ms;
+        std::sort(v.begin(), v.end());
+        auto q = [&](double f) { return v[std::min(v.size() - 1, (size_t)(f * (double)(v.size() - 1) + 0.5))]; };
+        out->p50_ms = q(0.50);
+        out->p99_ms = q(0.99);
+        out->max_ms = v.back();
+    }
+    return PE_OK;
+}
+
+extern "C" void poly_eval_server_destroy(pe_server *S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (uint32_t i = 0; i < S->nslots; ++i) {
+        Slot &s = S->slots[i];
+        if (s.staging) cudaFreeHost(s.staging);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.st) cudaStreamDestroy(s.st);
+    }
+    for (auto &kv : S->store) poly_eval_destroy(kv.second.poly);
+    for (SrvRequest *r : S->backlog) delete r;
+    delete S;
+}
