@@ -284,9 +284,10 @@ typedef struct {
     uint64_t T;
     uint64_t t0;
     uint64_t *out;
-    uint64_t *new_resident_id; /* optional: with poly_desc, receives the id under which the uploaded
-                                  polynomial stays resident for later requests (evicted least
-                                  recently used first when memory is needed) */
+    uint64_t *new_resident_id; /* optional: with poly_desc, receives (at submit) the id under which
+                                  the uploaded polynomial stays resident; requests may use it once
+                                  this request's ticket has completed (least recently used
+                                  residents are evicted first when memory is needed) */
 } pe_request;
 
 typedef struct {
@@ -305,6 +306,9 @@ pe_status poly_eval_server_submit(pe_server *srv, const pe_request *req, uint64_
 /* PE_OK when done (result in req->out), PE_PENDING / PE_ERR_TIMEOUT otherwise. */
 pe_status poly_eval_server_poll(pe_server *srv, uint64_t ticket, int64_t timeout_us);
 pe_status poly_eval_server_stats(pe_server *srv, pe_server_stats *stats);
+/* Stops (paused = 1) or resumes (0) the forming of new epochs; epochs already
+ * in flight complete and submissions keep queueing up to max_queue. */
+pe_status poly_eval_server_pause(pe_server *srv, int paused);
 void poly_eval_server_destroy(pe_server *srv);
 
 /* -------------------------------------------------------------------------

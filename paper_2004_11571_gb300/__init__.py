@@ -132,6 +132,7 @@ def lib():
             "poly_eval_server_poll": (st, [_vp, _u64, ctypes.c_int64]),
             "poly_eval_server_stats": (st, [_vp, ctypes.POINTER(_ServerStats)]),
             "poly_eval_server_destroy": (None, [_vp]),
+            "poly_eval_server_pause": (st, [_vp, ctypes.c_int]),
             "poly_eval_modmul_peak": (st, [ctypes.c_int, _u64, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]),
         }
@@ -363,6 +364,9 @@ class Server:
             return st
         self._keep.pop(int(ticket), None)
         _check(st)
+
+    def pause(self, paused: bool = True):
+        _check(lib().poly_eval_server_pause(self._h, 1 if paused else 0))
 
     def stats(self) -> dict:
         s = _ServerStats()

@@ -35,7 +35,7 @@ struct SrvRequest {
     uint64_t T = 0, t0 = 0;
     uint64_t *out = nullptr;
     bool out_pinned = false;
-    uint64_t *new_id_out = nullptr;
+    uint64_t reserved_id = 0;         // resident id of an upload, assigned at submit
     Clock::time_point submitted;
     pe_poly *poly = nullptr;          // once admitted
     uint64_t used_id = 0;
@@ -87,6 +87,7 @@ struct pe_server {
     uint32_t nslots = 0;
     std::thread worker;
     bool stop = false;
+    bool paused = false;
     // statistics
     uint64_t submitted = 0, completed = 0, rejected = 0, epochs = 0, evictions = 0;
     std::vector<double> lat_ms;
@@ -165,7 +166,7 @@ struct pe_server {
         {
             std::lock_guard<std::mutex> lk(mu);
             uint64_t need = 0;
-            while (!backlog.empty() && take.size() < cfg.max_epoch_jobs) {
+            while (!paused && !backlog.empty() && take.size() < cfg.max_epoch_jobs) {
                 SrvRequest *r = backlog.front();
                 uint64_t add = 0;
                 if (r->resident_id) {
@@ -221,7 +222,7 @@ struct pe_server {
                     continue;
                 }
                 std::lock_guard<std::mutex> lk(mu);
-                const uint64_t id = next_id++;
+                const uint64_t id = r->reserved_id;
                 Resident res;
                 res.poly = P;
                 res.bytes = P->device_bytes();
@@ -231,7 +232,6 @@ struct pe_server {
                 resident_bytes += res.bytes;
                 r->poly = P;
                 r->used_id = id;
-                if (r->new_id_out) *r->new_id_out = id;
             }
             ok.push_back(r);
         }
@@ -398,7 +398,6 @@ extern "C" pe_status poly_eval_server_submit(pe_server *S, const pe_request *req
     r->T = req->T;
     r->t0 = req->t0;
     r->out = req->out;
-    r->new_id_out = req->new_resident_id;
     cudaPointerAttributes a{};
     r->out_pinned = cudaPointerGetAttributes(&a, req->out) == cudaSuccess && a.type == cudaMemoryTypeHost;
     cudaGetLastError();
@@ -453,6 +452,10 @@ extern "C" pe_status poly_eval_server_submit(pe_server *S, const pe_request *req
         return PE_ERR_ADMISSION;
     }
     r->ticket = S->next_ticket++;
+    if (!r->resident_id) {
+        r->reserved_id = S->next_id++;
+        if (req->new_resident_id) *req->new_resident_id = r->reserved_id;
+    }
     S->status[r->ticket] = PE_PENDING;
     S->backlog.push_back(r);
     ++S->submitted;
@@ -513,12 +516,27 @@ extern "C" pe_status poly_eval_server_stats(pe_server *S, pe_server_stats *out)
     return PE_OK;
 }
 
+extern "C" pe_status poly_eval_server_pause(pe_server *S, int paused)
+{
+    if (!S) {
+        set_error("NULL server");
+        return PE_ERR_ARG;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->paused = paused != 0;
+    }
+    S->cv_work.notify_all();
+    return PE_OK;
+}
+
 extern "C" void poly_eval_server_destroy(pe_server *S)
 {
     if (!S) return;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stop = true;
+        S->paused = false;
     }
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();

@@ -55,7 +55,7 @@ def test_alone_and_in_mix_are_identical():
     for t in tickets:
         assert srv.poll(t) == 0
     for (w, beta, r, poly, out) in reqs:
-        if w is a:
+        if w is a and beta is a.beta:                # the alone request again, resident or re-uploaded
             assert np.array_equal(out, out_alone)
         else:
             wb = wl.Workload(p=w.p, n=w.n, coeffs=w.coeffs, exps=w.exps, beta=beta, T=w.T)
@@ -74,7 +74,7 @@ def test_alone_and_in_mix_are_identical():
 def test_resident_reuse_ids_backpressure_and_eviction():
     p = wl.random_prime(62, 5)
     ws = [wl.make_uniform(n=7, s=20_000, p=p, deg12=10, deg_rest=8, T=64, seed=k) for k in range(6)]
-    srv = pe.Server(mem_cap_bytes=24 << 20, max_queue=4, streams=1, max_epoch_jobs=2)
+    srv = pe.Server(mem_cap_bytes=6 << 20, max_queue=4, streams=1, max_epoch_jobs=2)
     outs, tickets, ids = [], [], []
     for w in ws[:3]:
         o = _out(w, _G(w), False)
@@ -94,7 +94,8 @@ def test_resident_reuse_ids_backpressure_and_eviction():
     assert srv.poll(t2) == 0
     wb = wl.Workload(p=w.p, n=w.n, coeffs=w.coeffs, exps=w.exps, beta=nb, T=w.T)
     assert np.array_equal(o2, oracle.eval_direct(wb)[1])
-    # backpressure: a full backlog refuses with PE_ERR_ADMISSION
+    # backpressure: while paused, a full backlog refuses with PE_ERR_ADMISSION
+    srv.pause(True)
     refused = 0
     pending = []
     for k in range(40):
@@ -104,11 +105,18 @@ def test_resident_reuse_ids_backpressure_and_eviction():
         except pe.PolyEvalError as e:
             assert e.status == pe.PE_ERR_ADMISSION
             refused += 1
+    assert len(pending) == 4 and refused == 36
+    assert srv.poll(pending[0], 0) == pe.PE_PENDING
+    srv.pause(False)
     for t in pending:
         assert srv.poll(t) == 0
+    for k in range(12):                              # more uploads than the 6 MB cap holds
+        w = ws[k % 6]
+        t, _ = srv.submit(w.beta, w.T, _out(w, _G(w), False), poly=(w.p, w.coeffs, w.exps))
+        assert srv.poll(t) == 0
     st = srv.stats()
-    assert refused > 0 and st["rejected"] >= refused
-    assert st["evictions"] > 0                      # 24 MB cap forces least-recently-used eviction
+    assert st["rejected"] >= refused
+    assert st["evictions"] > 0                      # least-recently-used residents make room
     with pytest.raises(pe.PolyEvalError) as e:
         srv.submit(ws[0].beta, 4, np.zeros((4, 10), np.uint64), resident_id=10_000)
     assert e.value.status == 10
