@@ -46,8 +46,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="large", choices=["large", "tiny", "width62", "width50", "batched"])
+    ap.add_argument("--config", default="large",
+                    choices=["large", "tiny", "width62", "width50", "batched", "served"])
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-burst", type=int, default=1500)
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -278,13 +283,20 @@ def run_ours(args):
             "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_stride)
-    print(json.dumps(line), flush=True)
     poly.close()
+    if world == 1 and not args.no_extras:
+        del out, flush
+        torch.cuda.empty_cache()
+        bargs = argparse.Namespace(**vars(args))
+        bargs.steps, bargs.warmup = 4, 2
+        line["batched"] = run_batched(bargs, print_line=False)
+        line["served"] = run_served(args)
+    print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def run_batched(args):
+def run_batched(args, print_line=True):
     """Config of 512 independent polynomials: one CUDA-graph launch of the
     persistent kernel vs a loop of per-polynomial poly_eval_run calls."""
     import torch
@@ -333,8 +345,20 @@ def run_batched(args):
     clk = clocks.stop()
     v_batch = tp / (statistics.mean(ms_batch) * 1e-3)
     v_loop = tp / (statistics.mean(ms_loop) * 1e-3)
+    launches_loop = sum(p.launches_per_run(w.T) for p, w in zip(polys, ws))
+    batch.close()
+    for p in polys:
+        p.close()
     if rank != 0:
-        return
+        return None
+    summary = {"workload": f"{len(ws)} polynomials: n 6..12, s log-uniform 1e3..1e6, D 5..60, "
+                           "T in {64,256,1024,2048}, 50/62-bit primes",
+               "term_points": tp, "batched_term_points_per_s": v_batch, "ms_per_launch": statistics.mean(ms_batch),
+               "plain_loop_term_points_per_s": v_loop, "plain_loop_ms": statistics.mean(ms_loop),
+               "batched_over_plain_loop": v_batch / v_loop, "launches_batched": 3,
+               "launches_plain_loop": launches_loop}
+    if not print_line:
+        return summary
     line = {"metric": "term-point evaluations/s (batched)", "value": v_batch * world, "unit": "term-points/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms_batch),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -347,6 +371,151 @@ def run_batched(args):
             "batched_over_plain_loop": v_batch / v_loop, "gpu_launches": 2 * args.steps,
             "host_seconds": {"generate": t_gen, "create": t_create, "plan_and_capture": t_plan}}
     print(json.dumps(line), flush=True)
+    return summary
+
+
+class PinnedRing:
+    """Page-locked host output buffers handed out in FIFO order."""
+
+    def __init__(self, nbytes):
+        import torch
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True).numpy()
+        self.cap = nbytes
+        self.head = 0
+        self.regions = []   # (start, end, ticket) in allocation order
+
+    def alloc(self, size, wait_oldest):
+        size = (size + 255) // 256 * 256
+        if size > self.cap:
+            raise ValueError("output larger than the ring")
+        while True:
+            if not self.regions:
+                self.head = 0
+                tail = 0
+            else:
+                tail = self.regions[0][0]
+            if self.head >= tail:
+                if self.cap - self.head >= size:
+                    return self.head
+                if tail >= size and (not self.regions or self.regions[0][0] >= size):
+                    return 0
+            elif tail - self.head >= size:
+                return self.head
+            wait_oldest()
+
+    def commit(self, start, size, ticket):
+        size = (size + 255) // 256 * 256
+        self.regions.append((start, start + size, ticket))
+        self.head = start + size
+
+    def view(self, start, shape):
+        n = shape[0] * shape[1] * 8
+        return self.buf[start:start + n].view(np.uint64).reshape(shape)
+
+
+def run_served(args, pool=None):
+    """Served workload: requests drawn from the batched mixture (30% reuse a
+    resident polynomial at a new beta).  Three measurements: a burst submitted
+    back to back (throughput at saturation), the same requests through the plain
+    path one by one (create, run into host memory, destroy), and a Poisson
+    stream at the configured rate (latency)."""
+    import torch
+    import paper_2004_11571_gb300 as pe
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if pool is None:
+        pool = wl.config_batched(seed=wl.SEED_SERVE, count=args.batch_count)
+    G = [int(len(np.unique(w.exps[:, 0].astype(np.int64) * 65536 + w.exps[:, 1]))) for w in pool]
+    ring = PinnedRing(6 << 30)
+
+    def drive(reqs, srv, paced):
+        ids, inflight = {}, []
+        start = time.perf_counter()
+        tp = 0.0
+
+        def wait_oldest():
+            s0, e0, t = ring.regions.pop(0)
+            srv.poll(t)
+
+        for (ts, k, beta) in reqs:
+            w = pool[k]
+            if paced:
+                delay = start + ts - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            shape = (w.T, G[k])
+            off = ring.alloc(shape[0] * shape[1] * 8, wait_oldest)
+            out = ring.view(off, shape)
+            ticket = None
+            if beta is not None and k in ids:
+                try:
+                    ticket, _ = srv.submit(beta, w.T, out, resident_id=ids[k])
+                except pe.PolyEvalError:
+                    ticket = None
+            while ticket is None:
+                try:
+                    ticket, nid = srv.submit(w.beta if beta is None else beta, w.T, out,
+                                             poly=(w.p, w.coeffs, w.exps))
+                    ids[k] = nid
+                except pe.PolyEvalError as e:
+                    if e.status != pe.PE_ERR_ADMISSION:
+                        raise
+                    if ring.regions:
+                        wait_oldest()
+                    else:
+                        time.sleep(0.001)
+            ring.commit(off, shape[0] * shape[1] * 8, ticket)
+            tp += w.s * w.T
+        while ring.regions:
+            wait_oldest()
+        return time.perf_counter() - start, tp
+
+    reqs = wl.served_requests(seed=wl.SEED_SERVE, rate=args.serve_rate, duration=args.serve_seconds, pool=pool)
+    burst = reqs[:args.serve_burst]
+    # (1) burst: throughput at saturation
+    srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
+    drive(burst[:50], srv, False)                      # warm-up
+    srv.close()
+    srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
+    t_burst, tp_burst = drive(burst, srv, False)
+    st_burst = srv.stats()
+    srv.close()
+    # (2) the plain path, one request at a time
+    polys = {}
+    t0 = time.perf_counter()
+    tp_plain = 0.0
+    for (ts, k, beta) in burst:
+        w = pool[k]
+        out = ring.view(0, (w.T, G[k]))
+        if beta is None or k not in polys:
+            if k in polys:
+                polys[k].close()
+            polys[k] = pe.Poly.from_workload(w)
+        polys[k].run(w.beta if beta is None else beta, w.T, 1, out=out)
+        tp_plain += w.s * w.T
+    t_plain = time.perf_counter() - t0
+    for p in polys.values():
+        p.close()
+    # (3) Poisson stream at the configured rate
+    srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
+    t_pois, tp_pois = drive(reqs, srv, True)
+    st_pois = srv.stats()
+    srv.close()
+    return {
+        "workload": f"requests from the {len(pool)}-polynomial batched mixture, 30% reuse a resident "
+                    "polynomial at a new beta, 40 GB resident cap",
+        "burst": {"requests": len(burst), "seconds": t_burst, "term_points_per_s": tp_burst / t_burst,
+                  "requests_per_s": len(burst) / t_burst, "p50_ms": st_burst["p50_ms"],
+                  "p99_ms": st_burst["p99_ms"], "epochs": st_burst["epochs"], "rejected": st_burst["rejected"]},
+        "plain_per_request": {"requests": len(burst), "seconds": t_plain, "term_points_per_s": tp_plain / t_plain,
+                              "requests_per_s": len(burst) / t_plain},
+        "served_over_plain": (tp_burst / t_burst) / (tp_plain / t_plain),
+        "poisson": {"rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "requests": len(reqs),
+                    "completed": st_pois["completed"], "achieved_requests_per_s": len(reqs) / t_pois,
+                    "goodput_term_points_per_s": tp_pois / t_pois, "p50_ms": st_pois["p50_ms"],
+                    "p99_ms": st_pois["p99_ms"], "max_ms": st_pois["max_ms"], "rejected": st_pois["rejected"],
+                    "evictions": st_pois["evictions"], "epochs": st_pois["epochs"]},
+    }
 
 
 def main():
@@ -355,6 +524,8 @@ def main():
         run_reference(args)
     elif args.config == "batched":
         run_batched(args)
+    elif args.config == "served":
+        print(json.dumps({"metric": "served", **run_served(args)}), flush=True)
     else:
         run_ours(args)
 

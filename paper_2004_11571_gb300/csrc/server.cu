@@ -206,21 +206,42 @@ struct pe_server {
             }
         }
         if (take.empty()) return false;
-        // Upload new polynomials (outside the lock).
-        std::vector<SrvRequest *> ok;
-        for (SrvRequest *r : take) {
-            if (!r->resident_id) {
+        // Upload new polynomials (outside the lock), several at a time: host
+        // packing dominates an upload, and the host has cores to spare.
+        std::vector<pe_poly *> made(take.size(), nullptr);
+        std::vector<int> made_st(take.size(), PE_OK);
+        std::vector<size_t> todo;
+        for (size_t j = 0; j < take.size(); ++j)
+            if (!take[j]->resident_id) todo.push_back(j);
+        const size_t nthr = std::min<size_t>(todo.size(), 8);
+        auto upload = [&](size_t first) {
+            cudaSetDevice(device);
+            for (size_t t = first; t < todo.size(); t += nthr) {
+                SrvRequest *r = take[todo[t]];
                 r->desc.coeffs = r->coeffs.data();
                 r->desc.exps = r->exps.data();
-                pe_poly *P = nullptr;
-                const pe_status st = poly_eval_create(&r->desc, &P);
+                made_st[todo[t]] = poly_eval_create(&r->desc, &made[todo[t]]);
                 std::vector<uint8_t>().swap(r->exps);
                 std::vector<uint64_t>().swap(r->coeffs);
-                if (st != PE_OK) {
+            }
+        };
+        if (nthr <= 1) {
+            if (nthr == 1) upload(0);
+        } else {
+            std::vector<std::thread> th;
+            for (size_t i = 0; i < nthr; ++i) th.emplace_back(upload, i);
+            for (std::thread &x : th) x.join();
+        }
+        std::vector<SrvRequest *> ok;
+        for (size_t j = 0; j < take.size(); ++j) {
+            SrvRequest *r = take[j];
+            if (!r->resident_id) {
+                if (made_st[j] != PE_OK) {
                     std::vector<SrvRequest *> one{r};
-                    fail(one, st);
+                    fail(one, made_st[j]);
                     continue;
                 }
+                pe_poly *P = made[j];
                 std::lock_guard<std::mutex> lk(mu);
                 const uint64_t id = r->reserved_id;
                 Resident res;
