@@ -137,7 +137,8 @@ pe_status poly_eval_groups(const pe_poly *poly, uint64_t *G, uint32_t *keys);
 pe_status poly_eval_run(pe_poly *poly, const uint64_t *beta, uint64_t T, uint64_t t0,
                         uint64_t *out, void *stream);
 
-/* Frees the handle and its device memory (NULL is a no-op). */
+/* Waits for the device to finish queued work (like cudaFree), then frees the
+ * handle and returns its device memory to the library's pool (NULL: no-op). */
 void poly_eval_destroy(pe_poly *poly);
 
 /* Message for the last failed call on this thread ("" if none). */

@@ -48,6 +48,27 @@ ModCtx make_modctx(uint64_t p)
     return m;
 }
 
+cudaStream_t alloc_stream()
+{
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {nullptr};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[dev]) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    }
+    return streams[dev];
+}
+
+void destroy_idle(pe_poly *P) { delete P; }
+
 int num_sms()
 {
     static int n = 0;
@@ -457,7 +478,14 @@ extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
     return PE_OK;
 }
 
-extern "C" void poly_eval_destroy(pe_poly *P) { delete P; }
+// Waits for the device (as cudaFree would) so that no queued run can still
+// read the polynomial's memory, then returns that memory to the pool.
+extern "C" void poly_eval_destroy(pe_poly *P)
+{
+    if (!P) return;
+    cudaDeviceSynchronize();
+    delete P;
+}
 
 extern "C" pe_status poly_eval_groups(const pe_poly *P, uint64_t *G, uint32_t *keys)
 {
@@ -606,6 +634,9 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
         return PE_ERR_ARG;
     }
     cudaStream_t cs = (cudaStream_t)stream;
+    // Buffers replaced below (plans, start values, output scratch) are freed on
+    // the allocation stream only after the previous run has finished with them.
+    if (P->last_use) cudaStreamWaitEvent(alloc_stream(), P->last_use, 0);
     Tiles t;
     if ((st = plan_for(P, T, &t)) != PE_OK) return st;
     cudaPointerAttributes attr{};
@@ -670,6 +701,9 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
     if ((e = launch_stepB((int)t.K, P->variant, J0, P->plan.U * P->plan.Q, J1, n1, (int)t.wpb, cs)) != cudaSuccess)
         return cuda_fail(e, "Step B");
     mark(3);
+    if (!P->last_use && (e = cudaEventCreateWithFlags(&P->last_use, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "event");
+    if ((e = cudaEventRecord(P->last_use, cs)) != cudaSuccess) return cuda_fail(e, "event");
     if (!dev_out) {
         if ((e = cudaMemcpyAsync(out, out_dev, T * P->G * 8, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
             return cuda_fail(e, "copy back");

@@ -399,7 +399,12 @@ extern "C" pe_status poly_eval_batch_set_beta(pe_batch *B, size_t j, const uint6
     return PE_OK;
 }
 
-extern "C" void poly_eval_batch_destroy(pe_batch *B) { delete B; }
+extern "C" void poly_eval_batch_destroy(pe_batch *B)
+{
+    if (!B) return;
+    cudaDeviceSynchronize();   // a launched graph may still be running
+    delete B;
+}
 
 extern "C" pe_status poly_eval_batch(const pe_job *jobs, size_t njobs, void *stream)
 {

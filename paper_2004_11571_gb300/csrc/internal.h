@@ -13,6 +13,14 @@ namespace pe {
 void set_error(const char *fmt, ...);
 pe_status cuda_fail(cudaError_t e, const char *what);
 
+// The library's allocation stream on the current device.  Buffers come from
+// the device's stream-ordered memory pool (kept cached: release threshold at
+// its maximum), so allocating and freeing never synchronizes the device.  A
+// buffer is freed only once no queued work can still use it: callers of the
+// public destroy functions are synchronized first, the server frees what its
+// completed epochs released.
+cudaStream_t alloc_stream();
+
 // Owned device allocation that only grows.
 struct DevBuf {
     void *p = nullptr;
@@ -23,7 +31,7 @@ struct DevBuf {
     ~DevBuf() { release(); }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, alloc_stream());
         p = nullptr;
         bytes = 0;
     }
@@ -32,7 +40,9 @@ struct DevBuf {
         if (n <= bytes && p) return cudaSuccess;
         release();
         if (n == 0) n = 16;
-        cudaError_t e = cudaMalloc(&p, n);
+        cudaStream_t s = alloc_stream();
+        cudaError_t e = cudaMallocAsync(&p, n, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // usable from any stream
         if (e != cudaSuccess) {
             p = nullptr;
             return e;
@@ -122,9 +132,11 @@ struct pe_poly {
     bool timing = false;
     std::vector<cudaEvent_t> events;   // 4 per timed run
     size_t events_used = 0;
+    cudaEvent_t last_use = nullptr;    // end of the latest run; frees of this handle's buffers wait for it
     ~pe_poly()
     {
         for (cudaEvent_t e : events) cudaEventDestroy(e);
+        if (last_use) cudaEventDestroy(last_use);
     }
     uint64_t device_bytes() const
     {
@@ -148,4 +160,6 @@ void fill_job(StepBJob &J, pe_poly *P, const PlanHost &ph, const uint32_t *cs, c
 // Fills a Step B job description from a poly and its current plan.
 StepBJob make_job(pe_poly *poly, const Plan &pl, uint64_t t0, uint64_t *out_dev, bool fused);
 pe_status check_beta(const pe_poly *poly, const uint64_t *beta, BetaArg *arg);
+// Frees a polynomial whose device work is known to have completed (no device synchronization).
+void destroy_idle(pe_poly *poly);
 }  // namespace pe

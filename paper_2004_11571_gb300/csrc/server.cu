@@ -117,7 +117,7 @@ struct pe_server {
             Resident r = store[victim];
             store.erase(victim);
             resident_bytes -= r.bytes;
-            poly_eval_destroy(r.poly);
+            destroy_idle(r.poly);          // refs == 0: its last epoch has completed
             ++evictions;
         }
         return true;
@@ -388,7 +388,7 @@ extern "C" pe_status poly_eval_server_register(pe_server *S, const pe_poly_desc 
     if (st != PE_OK) return st;
     std::lock_guard<std::mutex> lk(S->mu);
     if (!S->make_room(P->device_bytes())) {
-        poly_eval_destroy(P);
+        destroy_idle(P);
         set_error("resident store is full");
         return PE_ERR_ADMISSION;
     }
@@ -567,7 +567,8 @@ extern "C" void poly_eval_server_destroy(pe_server *S)
         if (s.done) cudaEventDestroy(s.done);
         if (s.st) cudaStreamDestroy(s.st);
     }
-    for (auto &kv : S->store) poly_eval_destroy(kv.second.poly);
+    cudaDeviceSynchronize();
+    for (auto &kv : S->store) destroy_idle(kv.second.poly);
     for (SrvRequest *r : S->backlog) delete r;
     delete S;
 }

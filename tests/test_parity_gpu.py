@@ -206,3 +206,26 @@ def test_full_size_configs_sampled(name):
     rows, cols = _sample_cells(w, cells.G, 48, 1)
     want = cells(rows + w.t0, cols)
     assert np.array_equal(outs[0][rows, cols], want)
+
+
+def test_replanning_while_previous_run_is_in_flight():
+    # Runs with different T on two streams re-plan the handle; buffers of the
+    # earlier, still-running launch must not be reused under it.
+    w = wl.make_zipf(n=7, s=200_000, p=P62, deg12=30, deg_rest=9, T=700, seed=23)
+    cells = oracle.CellOracle(w)
+    poly = pe.Poly.from_workload(w)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for k, T in enumerate([700, 96, 512, 33, 700]):
+        st = s1 if k % 2 == 0 else s2
+        with torch.cuda.stream(st):
+            o = torch.empty((T, poly.G), dtype=torch.int64, device="cuda")
+            poly.run(w.beta, T, 1 + k, out=o, stream=st)
+            outs.append((T, 1 + k, o, st))
+    torch.cuda.synchronize()
+    rnd = np.random.default_rng(4)
+    for T, t0, o, st in outs:
+        got = pe.to_u64(o)
+        r, g = rnd.integers(0, T, 12), rnd.integers(0, cells.G, 12)
+        assert np.array_equal(got[r, g], cells(r + t0, g))
+    poly.close()
