@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <mutex>
 #include <numeric>
+#include <thread>
 #include "internal.h"
 #include "kernels.h"
 #include "tune.h"
@@ -399,27 +400,58 @@ extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
         coeffs = hc.data();
         exps = he.data();
     }
-    // Validation.
+    // One pass (split over host threads for large inputs): reduced
+    // coefficients, the largest evaluated exponent, (d, e) keys, sortedness.
+    std::vector<uint64_t> key(s);
+    const unsigned nth = s >= (1u << 18) ? std::max(1u, std::min(8u, std::thread::hardware_concurrency())) : 1u;
+    std::vector<uint32_t> t_dmax(nth, 0);
+    std::vector<uint64_t> t_bad(nth, ~0ull);
+    std::vector<char> t_sorted(nth, 1);
+    auto scan = [&](unsigned t) {
+        const uint64_t i0 = s * t / nth, i1 = s * (t + 1) / nth;
+        uint32_t dm = 0;
+        uint64_t bad = ~0ull;
+        char srt = 1;
+        for (uint64_t i = i0; i < i1; ++i) {
+            if (coeffs[i] >= d->p && bad == ~0ull) bad = i;
+            const uint64_t k = ((uint64_t)read_exp(exps, w, i * n) << 32) | read_exp(exps, w, i * n + 1);
+            key[i] = k;
+            for (uint32_t j = 2; j < n; ++j) dm = std::max(dm, read_exp(exps, w, i * n + j));
+        }
+        for (uint64_t i = std::max<uint64_t>(i0, 1); i < i1; ++i)
+            if (key[i] > key[i - 1]) srt = 0;
+        t_dmax[t] = dm;
+        t_bad[t] = bad;
+        t_sorted[t] = srt;
+    };
+    auto parallel = [&](auto fn) {
+        if (nth == 1) {
+            fn(0u);
+            return;
+        }
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nth; ++t) th.emplace_back(fn, t);
+        for (std::thread &x : th) x.join();
+    };
+    parallel(scan);
     uint32_t dmax = 0;
-    for (uint64_t i = 0; i < s; ++i) {
-        if (coeffs[i] >= d->p) {
-            set_error("coefficient %llu of term %llu is not reduced mod p", (unsigned long long)coeffs[i],
-                      (unsigned long long)i);
+    bool sorted = true;
+    for (unsigned t = 0; t < nth; ++t) {
+        if (t_bad[t] != ~0ull) {
+            set_error("coefficient %llu of term %llu is not reduced mod p", (unsigned long long)coeffs[t_bad[t]],
+                      (unsigned long long)t_bad[t]);
             return PE_ERR_NOT_REDUCED;
         }
-        for (uint32_t j = 2; j < n; ++j) dmax = std::max(dmax, read_exp(exps, w, i * n + j));
+        dmax = std::max(dmax, t_dmax[t]);
+        sorted = sorted && t_sorted[t];
+        const uint64_t b = s * t / nth;   // thread boundaries
+        if (t && b && b < s && key[b] > key[b - 1]) sorted = false;
     }
     if (dmax > 0xffff) {
         set_error("exponent %u above 65535", dmax);
         return PE_ERR_EXP_RANGE;
     }
     // Group order: descending lex on (d, e); stable sort only when needed (Sect. 2.3).
-    std::vector<uint64_t> key(s);
-    bool sorted = true;
-    for (uint64_t i = 0; i < s; ++i) {
-        key[i] = ((uint64_t)read_exp(exps, w, i * n) << 32) | read_exp(exps, w, i * n + 1);
-        if (i && key[i] > key[i - 1]) sorted = false;
-    }
     std::vector<uint32_t> perm;
     if (!sorted) {
         perm.resize(s);
@@ -453,15 +485,19 @@ extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
     // Structure-of-arrays packing: coefficients, then E rows of exponents.
     std::vector<uint64_t> sc(s);
     std::vector<uint8_t> se((size_t)E * s * P->exp_bytes);
-    for (uint64_t i = 0; i < s; ++i) {
-        const uint64_t o = src(i);
-        sc[i] = coeffs[o];
-        for (uint32_t j = 0; j < E; ++j) {
-            const uint32_t x = read_exp(exps, w, o * n + 2 + j);
-            if (P->exp_bytes == 1) se[(size_t)j * s + i] = (uint8_t)x;
-            else ((uint16_t *)se.data())[(size_t)j * s + i] = (uint16_t)x;
+    auto pack = [&](unsigned t) {
+        const uint64_t i0 = s * t / nth, i1 = s * (t + 1) / nth;
+        for (uint64_t i = i0; i < i1; ++i) {
+            const uint64_t o = src(i);
+            sc[i] = coeffs[o];
+            if (P->exp_bytes == 1)
+                for (uint32_t j = 0; j < E; ++j) se[(size_t)j * s + i] = (uint8_t)read_exp(exps, w, o * n + 2 + j);
+            else
+                for (uint32_t j = 0; j < E; ++j)
+                    ((uint16_t *)se.data())[(size_t)j * s + i] = (uint16_t)read_exp(exps, w, o * n + 2 + j);
         }
-    }
+    };
+    parallel(pack);
     cudaError_t e;
     const size_t dp1 = dmax + 1;
     if ((e = P->coeffs.ensure(s * 8)) != cudaSuccess || (e = P->exps.ensure(se.size())) != cudaSuccess ||

@@ -198,9 +198,11 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
     std::vector<PlanHost> ph(njobs);
     std::vector<std::vector<uint32_t>> cs(njobs), cg(njobs);
     std::vector<int> var(njobs);
-    Layout L;
-    const size_t off_jobs = L.take(std::max<size_t>(njobs, 1) * sizeof(StepBJob));
-    const size_t off_pow = L.take(std::max<size_t>(njobs, 1) * sizeof(PowJob));
+    // Two regions: U (uploaded: descriptors, tables, betas, the queue) and S
+    // (scratch, written by the kernels before it is read; counters cleared).
+    Layout U, S;
+    const size_t off_jobs = U.take(std::max<size_t>(njobs, 1) * sizeof(StepBJob));
+    const size_t off_pow = U.take(std::max<size_t>(njobs, 1) * sizeof(PowJob));
     std::vector<size_t> o_cs(njobs), o_cg(njobs), o_unit(njobs), o_span(njobs), o_carry(njobs), o_chain(njobs),
         o_ptab(njobs), o_cnt(njobs);
     img.beta_off.assign(njobs, 0);
@@ -212,21 +214,15 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
         cs[j] = P->chunks.cs;
         cg[j] = P->chunks.cg;
         var[j] = resolve_variant(P, jobs[j].T);
-        o_cs[j] = L.take(cs[j].size() * 4);
-        o_cg[j] = L.take(std::max<size_t>(cg[j].size(), 1) * 4);
-        o_unit[j] = L.take(ph[j].unit.size() * 4);
-        o_span[j] = L.take(ph[j].span.size() * 4);
-        o_carry[j] = L.take(ph[j].carry_bytes());
-        o_chain[j] = L.take(ph[j].chain_bytes());
-        o_ptab[j] = L.take((size_t)std::max<uint32_t>(P->E, 1) * (P->dmax + 1) * 8);
-        img.beta_off[j] = L.take((size_t)std::max<uint32_t>(P->E, 1) * 8);
+        o_cs[j] = U.take(cs[j].size() * 4);
+        o_cg[j] = U.take(std::max<size_t>(cg[j].size(), 1) * 4);
+        o_unit[j] = U.take(ph[j].unit.size() * 4);
+        o_span[j] = U.take(ph[j].span.size() * 4);
+        img.beta_off[j] = U.take((size_t)std::max<uint32_t>(P->E, 1) * 8);
+        o_carry[j] = S.take(ph[j].carry_bytes());
+        o_chain[j] = S.take(ph[j].chain_bytes());
+        o_ptab[j] = S.take((size_t)std::max<uint32_t>(P->E, 1) * (P->dmax + 1) * 8);
     }
-    // Counters (and the queue head) in one contiguous region, cleared before each launch.
-    img.counters_off = L.off;
-    const size_t off_head = L.take(256);
-    for (size_t j = 0; j < njobs; ++j)
-        if (jobs[j].T && jobs[j].poly->G) o_cnt[j] = L.take(ph[j].counter_bytes());
-    img.counters_bytes = L.off - img.counters_off;
     // Items, ordered by decreasing cost (a slab-point of a K-term chunk costs K).
     std::vector<std::pair<double, uint2>> items;
     for (size_t j = 0; j < njobs; ++j) {
@@ -244,11 +240,27 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
         }
     }
     std::stable_sort(items.begin(), items.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
-    const size_t off_items = L.take(std::max<size_t>(items.size(), 1) * sizeof(uint2));
-    cudaError_t e = arena.ensure(L.off);
+    const size_t off_items = U.take(std::max<size_t>(items.size(), 1) * sizeof(uint2));
+    // Counters (and the queue head) in one contiguous scratch block, cleared before each launch.
+    const size_t cnt0 = S.off;
+    const size_t off_head = S.take(256);
+    for (size_t j = 0; j < njobs; ++j)
+        if (jobs[j].T && jobs[j].poly->G) o_cnt[j] = S.take(ph[j].counter_bytes());
+    const size_t cnt1 = S.off;
+    // Scratch offsets follow the uploaded region.
+    const size_t up = U.off;
+    for (size_t j = 0; j < njobs; ++j) {
+        o_carry[j] += up;
+        o_chain[j] += up;
+        o_ptab[j] += up;
+        o_cnt[j] += up;
+    }
+    img.counters_off = up + cnt0;
+    img.counters_bytes = cnt1 - cnt0;
+    cudaError_t e = arena.ensure(up + S.off);
     if (e != cudaSuccess) return cuda_fail(e, "batch arena");
     unsigned char *base = arena.as<unsigned char>();
-    img.host.assign(L.off, 0);
+    img.host.assign(up, 0);
     auto put = [&](size_t off, const void *src, size_t n) {
         if (n) memcpy(img.host.data() + off, src, n);
     };
@@ -283,7 +295,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
     img.d_jobs = (StepBJob *)(base + off_jobs);
     img.d_pow = (PowJob *)(base + off_pow);
     img.d_items = (uint2 *)(base + off_items);
-    img.d_head = (uint32_t *)(base + off_head);
+    img.d_head = (uint32_t *)(base + up + off_head);
     img.nitems = (uint32_t)items.size();
     img.njobs = (uint32_t)njobs;
     int bps = 0;
