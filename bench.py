@@ -33,11 +33,17 @@ import numpy as np  # noqa: E402
 
 import workloads as wl  # noqa: E402
 
-# 32-bit integer multiplies per term-point of the modular product (a 64x64
-# low product is 3, a high product 4, a full 128-bit product 4).
-MUL32_PER_TP = {"barrett64": 10, "mont64": 11}
-INT_MUL_PER_SM_PER_CLK = 64   # 32-bit IMAD issue rate per SM (CUDA throughput table)
+# Integer-multiply pipe issue slots per term-point of the modular product.
+# Lazy Barrett: quotient x1*w1 (wide) + hi(x1*w0) + hi(x0*w1); low products
+# x*w and q*p, each one wide and two low 32-bit multiplies.  A wide or high
+# multiply occupies the pipe for two slots, a low one for one: 3*2 + 2*2 + 4 = 14.
+# Montgomery: full x*y (4 wide), q = lo*p' (1 wide + 2 low), hi(q*p) (4 wide) = 20.
+SLOTS_PER_TP = {"barrett64": 14, "mont64": 20}
+INT_MUL_SLOTS_PER_SM_PER_CLK = 64   # 32-bit integer multiply-add issue rate per SM
 NUM_SMS = 152
+# DRAM bytes (read + write) of one Step B launch on the large workload, from one
+# ncu capture of the current kernel; None for other workloads.
+STEPB_TRAFFIC_LARGE = 148_010_240
 
 
 def parse():
@@ -251,13 +257,14 @@ def run_ours(args):
     mhz = clk["sm_mhz"] or 1920.0
     roof = None
     if variant != "fp64" and tps_b:
-        peak = NUM_SMS * INT_MUL_PER_SM_PER_CLK * mhz * 1e6 / 1e9
-        ach = tps_b * MUL32_PER_TP[vkey] / 1e9
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gmul32/s", "frac": ach / peak,
-                "traffic": None, "kernel": "pe::k_stepB",
-                "peak_source": f"{NUM_SMS} SMs x {INT_MUL_PER_SM_PER_CLK} int32 mul/clk x {mhz:.0f} MHz "
-                               "(median sampled SM clock)",
-                "algorithmic": f"{MUL32_PER_TP[vkey]} 32-bit multiplies per term-point x {s}x{T} term-points",
+        peak = NUM_SMS * INT_MUL_SLOTS_PER_SM_PER_CLK * mhz * 1e6 / 1e9
+        ach = tps_b * SLOTS_PER_TP[vkey] / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gslot/s", "frac": ach / peak,
+                "traffic": STEPB_TRAFFIC_LARGE if args.config == "large" and vkey == "barrett64" else None,
+                "kernel": "pe::k_stepB",
+                "peak_source": f"{NUM_SMS} SMs x {INT_MUL_SLOTS_PER_SM_PER_CLK} integer-multiply issue slots/clk x "
+                               f"{mhz:.0f} MHz (median sampled SM clock)",
+                "algorithmic": f"{SLOTS_PER_TP[vkey]} multiply-pipe slots per term-point x {s}x{T} term-points",
                 "stepB_ms": t_b / runs, "stepB_term_points_per_s": tps_b}
         try:
             cal, cal_mhz = pe.modmul_peak(vkey, w.p)
