@@ -199,7 +199,8 @@ def run_ours(args):
     variant = args.variant
     if variant == "auto" and args.config == "width50":
         variant = "fp64"
-    t0 = w.t0 + rank * w.T            # each rank: its own block of T points
+    from paper_2004_11571_gb300 import sharding
+    t0, _ = sharding.weak_block(int(w.T), w.t0, rank)   # each rank: its own block of T points
     poly = pe.Poly.from_workload(w, variant=variant)
     G, T, s = poly.G, int(w.T), w.s
     out = torch.empty((T, G), dtype=torch.int64, device="cuda")
@@ -318,7 +319,8 @@ def run_batched(args, print_line=True):
     polys = [pe.Poly.from_workload(w) for w in ws]
     t_create = time.perf_counter() - t_create
     outs = [torch.empty((w.T, p.G), dtype=torch.int64, device="cuda") for w, p in zip(ws, polys)]
-    t0s = [1 + rank * w.T for w in ws]
+    from paper_2004_11571_gb300 import sharding
+    t0s = [sharding.weak_block(int(w.T), 1, rank)[0] for w in ws]
     tp = sum(w.s * w.T for w in ws)
     t_plan = time.perf_counter()
     batch = pe.Batch([(p, w.beta, w.T, t0, o) for p, w, t0, o in zip(polys, ws, t0s, outs)])
