@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <mutex>
 #include <numeric>
+#include <memory>
 #include <thread>
 #include "internal.h"
 #include "kernels.h"
@@ -69,6 +70,52 @@ cudaStream_t alloc_stream()
 }
 
 void destroy_idle(pe_poly *P) { delete P; }
+
+// Page-locked staging buffers for uploads, reused across calls and threads.
+namespace {
+struct Staging {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_stage_mu;
+std::vector<Staging> g_stage_free;
+
+Staging stage_acquire(size_t n)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_stage_mu);
+        for (size_t i = 0; i < g_stage_free.size(); ++i)
+            if (g_stage_free[i].bytes >= n) {
+                Staging s = g_stage_free[i];
+                g_stage_free.erase(g_stage_free.begin() + i);
+                return s;
+            }
+    }
+    Staging s;
+    const size_t want = std::max<size_t>(n + n / 4, 1 << 20);
+    if (cudaMallocHost(&s.p, want) == cudaSuccess) s.bytes = want;
+    else {
+        cudaGetLastError();
+        s.p = nullptr;
+    }
+    return s;
+}
+
+void stage_release(Staging s)
+{
+    if (!s.p) return;
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    if (g_stage_free.size() < 16) {
+        g_stage_free.push_back(s);
+        return;
+    }
+    size_t small = 0;   // keep the 16 largest
+    for (size_t i = 1; i < g_stage_free.size(); ++i)
+        if (g_stage_free[i].bytes < g_stage_free[small].bytes) small = i;
+    if (g_stage_free[small].bytes < s.bytes) std::swap(g_stage_free[small], s);
+    cudaFreeHost(s.p);
+}
+}  // namespace
 
 int num_sms()
 {
@@ -402,7 +449,8 @@ extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
     }
     // One pass (split over host threads for large inputs): reduced
     // coefficients, the largest evaluated exponent, (d, e) keys, sortedness.
-    std::vector<uint64_t> key(s);
+    std::unique_ptr<uint64_t[]> key_buf(new uint64_t[std::max<uint64_t>(s, 1)]);   // not zero-filled
+    uint64_t *key = key_buf.get();
     const unsigned nth = s >= (1u << 18) ? std::max(1u, std::min(8u, std::thread::hardware_concurrency())) : 1u;
     std::vector<uint32_t> t_dmax(nth, 0);
     std::vector<uint64_t> t_bad(nth, ~0ull);
@@ -482,9 +530,15 @@ extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
     }
     if (s) P->group_off.push_back(s);
     P->G = P->keys.size() / 2;
-    // Structure-of-arrays packing: coefficients, then E rows of exponents.
-    std::vector<uint64_t> sc(s);
-    std::vector<uint8_t> se((size_t)E * s * P->exp_bytes);
+    // Structure-of-arrays packing, straight into page-locked staging:
+    // coefficients, then E rows of exponents.
+    const size_t se_bytes = (size_t)E * s * P->exp_bytes;
+    Staging stg = stage_acquire(s * 8 + se_bytes);
+    std::vector<uint8_t> fallback;
+    if (!stg.p) fallback.resize(s * 8 + se_bytes);
+    unsigned char *stage = stg.p ? (unsigned char *)stg.p : fallback.data();
+    uint64_t *sc = (uint64_t *)stage;
+    uint8_t *se = stage + s * 8;
     auto pack = [&](unsigned t) {
         const uint64_t i0 = s * t / nth, i1 = s * (t + 1) / nth;
         for (uint64_t i = i0; i < i1; ++i) {
@@ -494,22 +548,27 @@ extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
                 for (uint32_t j = 0; j < E; ++j) se[(size_t)j * s + i] = (uint8_t)read_exp(exps, w, o * n + 2 + j);
             else
                 for (uint32_t j = 0; j < E; ++j)
-                    ((uint16_t *)se.data())[(size_t)j * s + i] = (uint16_t)read_exp(exps, w, o * n + 2 + j);
+                    ((uint16_t *)se)[(size_t)j * s + i] = (uint16_t)read_exp(exps, w, o * n + 2 + j);
         }
     };
     parallel(pack);
     cudaError_t e;
     const size_t dp1 = dmax + 1;
-    if ((e = P->coeffs.ensure(s * 8)) != cudaSuccess || (e = P->exps.ensure(se.size())) != cudaSuccess ||
+    if ((e = P->coeffs.ensure(s * 8)) != cudaSuccess || (e = P->exps.ensure(se_bytes)) != cudaSuccess ||
         (e = P->mR.ensure(s * 8)) != cudaSuccess || (e = P->ptab.ensure((size_t)E * dp1 * 8)) != cudaSuccess) {
+        stage_release(stg);
         delete P;
         return cuda_fail(e, "device allocation");
     }
-    if ((s && (e = cudaMemcpy(P->coeffs.p, sc.data(), s * 8, cudaMemcpyHostToDevice)) != cudaSuccess) ||
-        (se.size() && (e = cudaMemcpy(P->exps.p, se.data(), se.size(), cudaMemcpyHostToDevice)) != cudaSuccess)) {
+    cudaStream_t as = alloc_stream();
+    if ((s && (e = cudaMemcpyAsync(P->coeffs.p, sc, s * 8, cudaMemcpyHostToDevice, as)) != cudaSuccess) ||
+        (se_bytes && (e = cudaMemcpyAsync(P->exps.p, se, se_bytes, cudaMemcpyHostToDevice, as)) != cudaSuccess) ||
+        (e = cudaStreamSynchronize(as)) != cudaSuccess) {
+        stage_release(stg);
         delete P;
         return cuda_fail(e, "uploading terms");
     }
+    stage_release(stg);
     *out = P;
     return PE_OK;
 }
