@@ -437,6 +437,8 @@ def run_served(args, pool=None):
     G = [int(len(np.unique(w.exps[:, 0].astype(np.int64) * 65536 + w.exps[:, 1]))) for w in pool]
     ring = PinnedRing(6 << 30)
 
+    submit_s = [0.0]
+
     def drive(reqs, srv, paced):
         ids, inflight = {}, []
         start = time.perf_counter()
@@ -456,6 +458,7 @@ def run_served(args, pool=None):
             off = ring.alloc(shape[0] * shape[1] * 8, wait_oldest)
             out = ring.view(off, shape)
             ticket = None
+            ts0 = time.perf_counter()
             if beta is not None and k in ids:
                 try:
                     ticket, _ = srv.submit(beta, w.T, out, resident_id=ids[k])
@@ -464,7 +467,7 @@ def run_served(args, pool=None):
             while ticket is None:
                 try:
                     ticket, nid = srv.submit(w.beta if beta is None else beta, w.T, out,
-                                             poly=(w.p, w.coeffs, w.exps))
+                                             poly=(w.p, w.coeffs, w.exps), borrow=True)
                     ids[k] = nid
                 except pe.PolyEvalError as e:
                     if e.status != pe.PE_ERR_ADMISSION:
@@ -473,6 +476,7 @@ def run_served(args, pool=None):
                         wait_oldest()
                     else:
                         time.sleep(0.001)
+            submit_s[0] += time.perf_counter() - ts0
             ring.commit(off, shape[0] * shape[1] * 8, ticket)
             tp += w.s * w.T
         while ring.regions:
@@ -507,6 +511,7 @@ def run_served(args, pool=None):
         p.close()
     # (3) Poisson stream at the configured rate
     srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
+    submit_s[0] = 0.0
     t_pois, tp_pois = drive(reqs, srv, True)
     st_pois = srv.stats()
     srv.close()
@@ -523,7 +528,10 @@ def run_served(args, pool=None):
                     "completed": st_pois["completed"], "achieved_requests_per_s": len(reqs) / t_pois,
                     "goodput_term_points_per_s": tp_pois / t_pois, "p50_ms": st_pois["p50_ms"],
                     "p99_ms": st_pois["p99_ms"], "max_ms": st_pois["max_ms"], "rejected": st_pois["rejected"],
-                    "evictions": st_pois["evictions"], "epochs": st_pois["epochs"]},
+                    "evictions": st_pois["evictions"], "epochs": st_pois["epochs"],
+                    "host_seconds": {"client_submit": submit_s[0], "worker_upload": st_pois["upload_s"],
+                                     "worker_plan": st_pois["plan_s"], "worker_launch": st_pois["launch_s"],
+                                     "worker_finish": st_pois["finish_s"], "gpu_busy": st_pois["busy_s"]}},
     }
 
 

@@ -77,6 +77,8 @@ typedef enum {
 /* pe_poly_desc.flags */
 #define PE_FLAG_DEVICE_PTRS 0x1u  /* coeffs and exps are device pointers */
 #define PE_FLAG_SORTED      0x2u  /* hint: terms already in descending (d, e) order */
+#define PE_FLAG_BORROW      0x4u  /* server submit: the arrays stay valid and unchanged until the
+                                     request's ticket completes, so they are not copied */
 
 #define PE_MAX_VARS 66            /* n <= 66, i.e. at most 64 evaluated variables */
 
@@ -297,6 +299,8 @@ typedef struct {
     double term_points;                 /* sum of s*T over completed requests */
     double busy_s;                      /* wall time with at least one epoch in flight */
     uint64_t resident_bytes, resident_polys, evictions;
+    double upload_s, plan_s, launch_s, finish_s;   /* worker time: uploads, batch planning,
+                                                      enqueueing, completing tickets */
 } pe_server_stats;
 
 pe_status poly_eval_server_create(const pe_server_cfg *cfg, pe_server **out);

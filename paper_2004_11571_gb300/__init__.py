@@ -34,7 +34,7 @@ STATUS = {0: "PE_OK", 1: "PE_ERR_ARG", 2: "PE_ERR_PRIME", 3: "PE_ERR_NOT_REDUCED
           5: "PE_ERR_NOMEM", 6: "PE_ERR_ADMISSION", 7: "PE_ERR_CUDA", 8: "PE_ERR_TIMEOUT", 9: "PE_PENDING",
           10: "PE_ERR_NOT_FOUND"}
 PE_OK, PE_PENDING, PE_ERR_TIMEOUT, PE_ERR_ADMISSION = 0, 9, 8, 6
-FLAG_DEVICE_PTRS, FLAG_SORTED = 0x1, 0x2
+FLAG_DEVICE_PTRS, FLAG_SORTED, FLAG_BORROW = 0x1, 0x2, 0x4
 
 
 class PolyEvalError(RuntimeError):
@@ -81,7 +81,8 @@ class _ServerStats(ctypes.Structure):
                 ("epochs", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("term_points", ctypes.c_double), ("busy_s", ctypes.c_double),
                 ("resident_bytes", ctypes.c_uint64), ("resident_polys", ctypes.c_uint64),
-                ("evictions", ctypes.c_uint64)]
+                ("evictions", ctypes.c_uint64), ("upload_s", ctypes.c_double), ("plan_s", ctypes.c_double),
+                ("launch_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -338,21 +339,24 @@ class Server:
         return int(rid.value)
 
     def submit(self, beta, T: int, out: np.ndarray, t0: int = 1, poly=None, resident_id: int = 0,
-               variant="auto"):
-        """poly = (p, coeffs, exps) uploads a new polynomial; returns (ticket, new_resident_id)."""
+               variant="auto", borrow: bool = False):
+        """poly = (p, coeffs, exps) uploads a new polynomial; returns (ticket, new_resident_id).
+        borrow=True: the arrays are not copied and must stay unchanged until the ticket completes."""
         b = np.ascontiguousarray(np.asarray(beta, dtype=np.uint64).reshape(-1))
         new_id = ctypes.c_uint64(0)
         desc_ref = None
         keep = None
         if poly is not None:
             desc, keep = _make_desc(int(poly[0]), poly[1], poly[2], variant, False)
+            if borrow:
+                desc.flags |= FLAG_BORROW
             desc_ref = ctypes.addressof(desc)
         req = _Request(desc_ref, int(resident_id), b.ctypes.data if b.size else None, int(T), int(t0),
                        out.ctypes.data, ctypes.addressof(new_id))
         t = ctypes.c_uint64()
         _check(lib().poly_eval_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
-        del keep, desc_ref
-        self._keep[int(t.value)] = out
+        del desc_ref
+        self._keep[int(t.value)] = (out, keep) if borrow else out
         return int(t.value), int(new_id.value)
 
     def poll(self, ticket: int, timeout_us: int = -1) -> int:

@@ -101,6 +101,35 @@ Staging stage_acquire(size_t n)
     return s;
 }
 
+std::vector<cudaStream_t> g_up_streams;   // idle upload streams (same mutex)
+
+// A non-blocking stream for one upload, from a pool (uploads on several host
+// threads then proceed in parallel instead of queueing on one stream).
+cudaStream_t upload_stream_acquire()
+{
+    {
+        std::lock_guard<std::mutex> lk(g_stage_mu);
+        if (!g_up_streams.empty()) {
+            cudaStream_t s = g_up_streams.back();
+            g_up_streams.pop_back();
+            return s;
+        }
+    }
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return s;
+}
+
+void upload_stream_release(cudaStream_t s)
+{
+    if (!s) return;
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    g_up_streams.push_back(s);
+}
+
 void stage_release(Staging s)
 {
     if (!s.p) return;
@@ -394,7 +423,9 @@ using namespace pe;
 
 extern "C" const char *poly_eval_last_error(void) { return g_err.c_str(); }
 
-extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
+extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out) { return create_poly(d, out, true); }
+
+pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_threads)
 {
     if (!out) {
         set_error("out is NULL");
@@ -451,7 +482,8 @@ extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
     // coefficients, the largest evaluated exponent, (d, e) keys, sortedness.
     std::unique_ptr<uint64_t[]> key_buf(new uint64_t[std::max<uint64_t>(s, 1)]);   // not zero-filled
     uint64_t *key = key_buf.get();
-    const unsigned nth = s >= (1u << 18) ? std::max(1u, std::min(8u, std::thread::hardware_concurrency())) : 1u;
+    const unsigned nth = host_threads && s >= (1u << 18)
+                             ? std::max(1u, std::min(8u, std::thread::hardware_concurrency())) : 1u;
     std::vector<uint32_t> t_dmax(nth, 0);
     std::vector<uint64_t> t_bad(nth, ~0ull);
     std::vector<char> t_sorted(nth, 1);
@@ -554,20 +586,23 @@ extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out)
     parallel(pack);
     cudaError_t e;
     const size_t dp1 = dmax + 1;
-    if ((e = P->coeffs.ensure(s * 8)) != cudaSuccess || (e = P->exps.ensure(se_bytes)) != cudaSuccess ||
-        (e = P->mR.ensure(s * 8)) != cudaSuccess || (e = P->ptab.ensure((size_t)E * dp1 * 8)) != cudaSuccess) {
+    cudaStream_t us = upload_stream_acquire();
+    if ((e = P->coeffs.ensure(s * 8, us)) != cudaSuccess || (e = P->exps.ensure(se_bytes, us)) != cudaSuccess ||
+        (e = P->mR.ensure(s * 8, us)) != cudaSuccess || (e = P->ptab.ensure((size_t)E * dp1 * 8, us)) != cudaSuccess) {
+        upload_stream_release(us);
         stage_release(stg);
         delete P;
         return cuda_fail(e, "device allocation");
     }
-    cudaStream_t as = alloc_stream();
-    if ((s && (e = cudaMemcpyAsync(P->coeffs.p, sc, s * 8, cudaMemcpyHostToDevice, as)) != cudaSuccess) ||
-        (se_bytes && (e = cudaMemcpyAsync(P->exps.p, se, se_bytes, cudaMemcpyHostToDevice, as)) != cudaSuccess) ||
-        (e = cudaStreamSynchronize(as)) != cudaSuccess) {
+    if ((s && (e = cudaMemcpyAsync(P->coeffs.p, sc, s * 8, cudaMemcpyHostToDevice, us)) != cudaSuccess) ||
+        (se_bytes && (e = cudaMemcpyAsync(P->exps.p, se, se_bytes, cudaMemcpyHostToDevice, us)) != cudaSuccess) ||
+        (e = cudaStreamSynchronize(us)) != cudaSuccess) {
+        upload_stream_release(us);
         stage_release(stg);
         delete P;
         return cuda_fail(e, "uploading terms");
     }
+    upload_stream_release(us);
     stage_release(stg);
     *out = P;
     return PE_OK;

@@ -35,14 +35,16 @@ struct DevBuf {
         p = nullptr;
         bytes = 0;
     }
-    cudaError_t ensure(size_t n)
+    // Allocates on `s` (the library stream by default) and waits for it, so the
+    // buffer is usable from any stream on return.
+    cudaError_t ensure(size_t n, cudaStream_t s = nullptr)
     {
         if (n <= bytes && p) return cudaSuccess;
         release();
         if (n == 0) n = 16;
-        cudaStream_t s = alloc_stream();
+        if (!s) s = alloc_stream();
         cudaError_t e = cudaMallocAsync(&p, n, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // usable from any stream
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             p = nullptr;
             return e;
@@ -162,4 +164,6 @@ StepBJob make_job(pe_poly *poly, const Plan &pl, uint64_t t0, uint64_t *out_dev,
 pe_status check_beta(const pe_poly *poly, const uint64_t *beta, BetaArg *arg);
 // Frees a polynomial whose device work is known to have completed (no device synchronization).
 void destroy_idle(pe_poly *poly);
+// poly_eval_create with control over host threads (the server parallelizes across uploads instead).
+pe_status create_poly(const pe_poly_desc *desc, pe_poly **out, bool host_threads);
 }  // namespace pe

@@ -92,6 +92,7 @@ struct pe_server {
     uint64_t submitted = 0, completed = 0, rejected = 0, epochs = 0, evictions = 0;
     std::vector<double> lat_ms;
     double term_points = 0.0, busy_s = 0.0;
+    double t_upload = 0.0, t_plan = 0.0, t_launch = 0.0, t_finish = 0.0;   // worker thread only
     Clock::time_point busy_since;
     int inflight = 0;
 
@@ -123,9 +124,16 @@ struct pe_server {
         return true;
     }
 
+    static double since(Clock::time_point a) { return std::chrono::duration<double>(Clock::now() - a).count(); }
+
     void finish(Slot &s)
     {
         const Clock::time_point now = Clock::now();
+        struct Acc {
+            double &t;
+            Clock::time_point a;
+            ~Acc() { t += since(a); }
+        } acc{t_finish, now};
         for (SrvRequest *r : s.reqs) {
             if (!r->out_pinned && r->out_bytes)
                 memcpy(r->out, (unsigned char *)s.staging + r->out_off, r->out_bytes);
@@ -206,6 +214,7 @@ struct pe_server {
             }
         }
         if (take.empty()) return false;
+        const Clock::time_point t_up0 = Clock::now();
         // Upload new polynomials (outside the lock), several at a time: host
         // packing dominates an upload, and the host has cores to spare.
         std::vector<pe_poly *> made(take.size(), nullptr);
@@ -218,9 +227,11 @@ struct pe_server {
             cudaSetDevice(device);
             for (size_t t = first; t < todo.size(); t += nthr) {
                 SrvRequest *r = take[todo[t]];
-                r->desc.coeffs = r->coeffs.data();
-                r->desc.exps = r->exps.data();
-                made_st[todo[t]] = poly_eval_create(&r->desc, &made[todo[t]]);
+                if (!(r->desc.flags & PE_FLAG_BORROW)) {
+                    r->desc.coeffs = r->coeffs.data();
+                    r->desc.exps = r->exps.data();
+                }
+                made_st[todo[t]] = create_poly(&r->desc, &made[todo[t]], false);
                 std::vector<uint8_t>().swap(r->exps);
                 std::vector<uint64_t>().swap(r->coeffs);
             }
@@ -256,7 +267,9 @@ struct pe_server {
             }
             ok.push_back(r);
         }
+        t_upload += since(t_up0);
         if (ok.empty()) return false;
+        const Clock::time_point t_pl0 = Clock::now();
         // Outputs, then the batch.
         size_t total = 0;
         for (SrvRequest *r : ok) {
@@ -291,6 +304,8 @@ struct pe_server {
             s.term_points += (double)r->poly->s * (double)r->T;
         }
         pe_status st = batch_build(jobs.data(), jobs.size(), s.arena, s.img);
+        t_plan += since(t_pl0);
+        const Clock::time_point t_la0 = Clock::now();
         if (st == PE_OK && (e = batch_enqueue(s.img, s.st)) != cudaSuccess) st = cuda_fail(e, "server epoch");
         for (size_t j = 0; st == PE_OK && j < ok.size(); ++j) {
             SrvRequest *r = ok[j];
@@ -307,6 +322,7 @@ struct pe_server {
         }
         s.reqs = ok;
         s.busy = true;
+        t_launch += since(t_la0);
         std::lock_guard<std::mutex> lk(mu);
         if (inflight++ == 0) busy_since = Clock::now();
         ++epochs;
@@ -432,9 +448,11 @@ extern "C" pe_status poly_eval_server_submit(pe_server *S, const pe_request *req
             return PE_ERR_ARG;
         }
         r->desc = d;
-        r->coeffs.assign(d.coeffs, d.coeffs + d.s);
         const uint8_t *e = (const uint8_t *)d.exps;
-        r->exps.assign(e, e + d.s * d.n * d.exp_bytes);
+        if (!(d.flags & PE_FLAG_BORROW)) {           // copy: the caller may reuse its arrays at once
+            r->coeffs.assign(d.coeffs, d.coeffs + d.s);
+            r->exps.assign(e, e + d.s * d.n * d.exp_bytes);
+        }
         n = d.n;
         uint64_t md = 0, me = 0;   // the groups lie in a (max d + 1) x (max e + 1) grid
         for (uint64_t i = 0; i < d.s; ++i) {
@@ -526,6 +544,10 @@ extern "C" pe_status poly_eval_server_stats(pe_server *S, pe_server_stats *out)
     out->resident_bytes = S->resident_bytes;
     out->resident_polys = S->store.size();
     out->evictions = S->evictions;
+    out->upload_s = S->t_upload;   // written by the worker; read without tearing on 64-bit hosts
+    out->plan_s = S->t_plan;
+    out->launch_s = S->t_launch;
+    out->finish_s = S->t_finish;
     if (!S->lat_ms.empty()) {
         std::vector<double> v = S->lat_ms;
         std::sort(v.begin(), v.end());

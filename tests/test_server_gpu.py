@@ -50,8 +50,8 @@ def test_alone_and_in_mix_are_identical():
         else:
             reqs.append((w, w.beta, None, (w.p, w.coeffs, w.exps), _out(w, _G(w), k % 2 == 0)))
     tickets = []
-    for w, beta, r, poly, out in reqs:
-        tickets.append(srv.submit(beta, w.T, out, poly=poly, resident_id=r or 0)[0])
+    for k, (w, beta, r, poly, out) in enumerate(reqs):
+        tickets.append(srv.submit(beta, w.T, out, poly=poly, resident_id=r or 0, borrow=k % 4 == 1)[0])
     for t in tickets:
         assert srv.poll(t) == 0
     for (w, beta, r, poly, out) in reqs:
