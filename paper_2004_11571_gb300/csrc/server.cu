@@ -1,15 +1,18 @@
 // Server: continuous batching of evaluation requests.
 //
 // Clients submit requests (a polynomial to upload, or one already resident,
-// with beta, T, t0 and a host output buffer) into a bounded backlog.  A worker
-// thread forms an epoch whenever one of its streams is free: it admits
-// backlog requests in arrival order while their device memory fits under the
-// cap (evicting resident polynomials least recently used first), uploads new
-// polynomials, plans the epoch as one batch (persistent queue kernel, see
-// batch.cu) into that stream's reusable arena and launches it.  Epochs on
-// different streams overlap on the GPU, so requests that arrive while others
-// run are admitted as soon as a stream and memory are free.  Results go back
-// with an asynchronous copy (page-locked outputs) or through a staging buffer.
+// with beta, T, t0 and a host output buffer).  Three stages run concurrently:
+//  * upload threads take requests with a new polynomial from the backlog in
+//    arrival order, admit them while their device memory fits under the cap
+//    (evicting unreferenced uploads least recently used first), build the
+//    polynomial on the device and move the request to the ready queue;
+//    requests on a resident polynomial are ready at submit;
+//  * the epoch thread, whenever one of its streams is free, packs ready
+//    requests into one batch (persistent queue kernel, see batch.cu) in that
+//    stream's reusable arena and launches it, so epochs on different streams
+//    overlap on the GPU and requests that arrive meanwhile join the next one;
+//  * completion: results go back by asynchronous copy into page-locked
+//    buffers (others through a staging buffer) and tickets are marked done.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -29,7 +32,7 @@ struct SrvRequest {
     uint64_t ticket = 0;
     uint64_t resident_id = 0;         // 0: upload `desc`
     pe_poly_desc desc{};
-    std::vector<uint64_t> coeffs;
+    std::vector<uint64_t> coeffs;     // copies, unless the caller lends its arrays
     std::vector<uint8_t> exps;
     std::vector<uint64_t> beta;
     uint64_t T = 0, t0 = 0;
@@ -37,17 +40,16 @@ struct SrvRequest {
     bool out_pinned = false;
     uint64_t reserved_id = 0;         // resident id of an upload, assigned at submit
     Clock::time_point submitted;
-    pe_poly *poly = nullptr;          // once admitted
-    uint64_t used_id = 0;
+    pe_poly *poly = nullptr;          // once on the device
+    uint64_t used_id = 0;             // store entry holding a reference for this request
     size_t out_off = 0, out_bytes = 0;
-    uint64_t g_est = 0;               // bound on the group count of an upload
 };
 
 struct Resident {
     pe_poly *poly = nullptr;
     uint64_t bytes = 0;
     uint64_t last_use = 0;
-    uint32_t refs = 0;                // admitted requests using it
+    uint32_t refs = 0;                // queued or running requests using it
     bool pinned = false;              // registered by the client: never evicted
 };
 
@@ -69,6 +71,8 @@ static uint64_t poly_bytes_estimate(const pe_poly_desc &d)
     return d.s * (8 + 8 + E * 2) + 4096;
 }
 
+static double since(Clock::time_point a) { return std::chrono::duration<double>(Clock::now() - a).count(); }
+
 }  // namespace pe
 
 using namespace pe;
@@ -77,28 +81,31 @@ struct pe_server {
     pe_server_cfg cfg{};
     int device = 0;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<SrvRequest *> backlog;
+    std::condition_variable cv_work, cv_done, cv_upload;
+    std::deque<SrvRequest *> backlog;   // new polynomials waiting for an upload thread
+    std::deque<SrvRequest *> ready;     // on the device, waiting for an epoch
     std::unordered_map<uint64_t, int> status;   // ticket -> PE_PENDING / PE_OK / error
     std::unordered_map<uint64_t, Resident> store;
     uint64_t next_ticket = 1, next_id = 1, use_clock = 0;
-    uint64_t resident_bytes = 0;
+    uint64_t resident_bytes = 0, reserved_bytes = 0;
     Slot slots[4];
     uint32_t nslots = 0;
     std::thread worker;
+    std::vector<std::thread> uploaders;
+    int uploading = 0;
     bool stop = false;
     bool paused = false;
     // statistics
     uint64_t submitted = 0, completed = 0, rejected = 0, epochs = 0, evictions = 0;
     std::vector<double> lat_ms;
     double term_points = 0.0, busy_s = 0.0;
-    double t_upload = 0.0, t_plan = 0.0, t_launch = 0.0, t_finish = 0.0;   // worker thread only
+    double t_upload = 0.0, t_plan = 0.0, t_launch = 0.0, t_finish = 0.0;
     Clock::time_point busy_since;
     int inflight = 0;
 
     uint64_t committed() const
     {
-        uint64_t b = resident_bytes;
+        uint64_t b = resident_bytes + reserved_bytes;
         for (uint32_t i = 0; i < nslots; ++i) b += slots[i].arena.bytes + slots[i].outs.bytes;
         return b;
     }
@@ -118,30 +125,95 @@ struct pe_server {
             Resident r = store[victim];
             store.erase(victim);
             resident_bytes -= r.bytes;
-            destroy_idle(r.poly);          // refs == 0: its last epoch has completed
+            destroy_idle(r.poly);          // refs == 0: the epochs that used it have completed
             ++evictions;
         }
         return true;
     }
 
-    static double since(Clock::time_point a) { return std::chrono::duration<double>(Clock::now() - a).count(); }
+    void release_ref(SrvRequest *r)    // with `mu` held
+    {
+        auto it = store.find(r->used_id);
+        if (it != store.end() && it->second.refs) it->second.refs--;
+    }
 
+    void fail_locked(SrvRequest *r, int code)
+    {
+        release_ref(r);
+        status[r->ticket] = code;
+        delete r;
+        cv_done.notify_all();
+        cv_upload.notify_all();
+    }
+
+    // ---------------------------------------------------------------- uploads
+    void upload_loop()
+    {
+        cudaSetDevice(device);
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv_upload.wait(lk, [&] { return stop || !backlog.empty(); });
+            if (backlog.empty()) {
+                if (stop) return;
+                continue;
+            }
+            SrvRequest *r = backlog.front();
+            const uint64_t need = poly_bytes_estimate(r->desc);
+            if (!make_room(need)) {
+                if (uploading == 0 && inflight == 0 && ready.empty()) {   // can never fit
+                    backlog.pop_front();
+                    ++rejected;
+                    fail_locked(r, PE_ERR_ADMISSION);
+                    continue;
+                }
+                cv_upload.wait_for(lk, std::chrono::milliseconds(1));     // wait for memory
+                continue;
+            }
+            backlog.pop_front();
+            reserved_bytes += need;
+            ++uploading;
+            lk.unlock();
+            const Clock::time_point t0 = Clock::now();
+            if (!(r->desc.flags & PE_FLAG_BORROW)) {
+                r->desc.coeffs = r->coeffs.data();
+                r->desc.exps = r->exps.data();
+            }
+            pe_poly *P = nullptr;
+            const pe_status st = create_poly(&r->desc, &P, false);
+            std::vector<uint8_t>().swap(r->exps);
+            std::vector<uint64_t>().swap(r->coeffs);
+            const double dt = since(t0);
+            lk.lock();
+            --uploading;
+            reserved_bytes -= need;
+            t_upload += dt;
+            if (st != PE_OK) {
+                fail_locked(r, st);
+                continue;
+            }
+            Resident res;
+            res.poly = P;
+            res.bytes = P->device_bytes();
+            res.refs = 1;
+            res.last_use = ++use_clock;
+            store[r->reserved_id] = res;
+            resident_bytes += res.bytes;
+            r->poly = P;
+            r->used_id = r->reserved_id;
+            ready.push_back(r);
+            cv_work.notify_one();
+        }
+    }
+
+    // ------------------------------------------------------------- completion
     void finish(Slot &s)
     {
         const Clock::time_point now = Clock::now();
-        struct Acc {
-            double &t;
-            Clock::time_point a;
-            ~Acc() { t += since(a); }
-        } acc{t_finish, now};
-        for (SrvRequest *r : s.reqs) {
-            if (!r->out_pinned && r->out_bytes)
-                memcpy(r->out, (unsigned char *)s.staging + r->out_off, r->out_bytes);
-        }
+        for (SrvRequest *r : s.reqs)
+            if (!r->out_pinned && r->out_bytes) memcpy(r->out, (unsigned char *)s.staging + r->out_off, r->out_bytes);
         std::lock_guard<std::mutex> lk(mu);
         for (SrvRequest *r : s.reqs) {
-            auto it = store.find(r->used_id);
-            if (it != store.end() && it->second.refs) it->second.refs--;
+            release_ref(r);
             status[r->ticket] = PE_OK;
             lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->submitted).count());
             ++completed;
@@ -151,126 +223,37 @@ struct pe_server {
         s.reqs.clear();
         s.busy = false;
         if (--inflight == 0) busy_s += std::chrono::duration<double>(now - busy_since).count();
+        t_finish += since(now);
         cv_done.notify_all();
+        cv_upload.notify_all();
     }
 
-    void fail(std::vector<SrvRequest *> &reqs, int code)
+    void fail_all(std::vector<SrvRequest *> &reqs, int code)
     {
         std::lock_guard<std::mutex> lk(mu);
-        for (SrvRequest *r : reqs) {
-            auto it = store.find(r->used_id);
-            if (it != store.end() && it->second.refs) it->second.refs--;
-            status[r->ticket] = code;
-            delete r;
-        }
+        for (SrvRequest *r : reqs) fail_locked(r, code);
         reqs.clear();
-        cv_done.notify_all();
     }
 
-    // Admits backlog requests into slot `s` and launches them as one epoch.
+    // ----------------------------------------------------------------- epochs
+    // Packs ready requests into slot `s` and launches them as one epoch.
     bool launch(Slot &s)
     {
-        std::vector<SrvRequest *> take;
+        std::vector<SrvRequest *> ok;
         {
             std::lock_guard<std::mutex> lk(mu);
             uint64_t need = 0;
-            while (!paused && !backlog.empty() && take.size() < cfg.max_epoch_jobs) {
-                SrvRequest *r = backlog.front();
-                uint64_t add = 0;
-                if (r->resident_id) {
-                    auto it = store.find(r->resident_id);
-                    if (it == store.end()) {
-                        status[r->ticket] = PE_ERR_NOT_FOUND;
-                        backlog.pop_front();
-                        delete r;
-                        cv_done.notify_all();
-                        continue;
-                    }
-                    r->poly = it->second.poly;
-                    add = r->T * r->poly->G * 8 + r->poly->s * 24 + r->T * 1024;
-                } else {
-                    add = poly_bytes_estimate(r->desc) + r->T * r->g_est * 8 + r->desc.s * 24 + r->T * 1024;
-                }
-                if (!make_room(need + add)) {
-                    if (take.empty() && inflight == 0) {   // can never fit
-                        status[r->ticket] = PE_ERR_ADMISSION;
-                        ++rejected;
-                        backlog.pop_front();
-                        delete r;
-                        cv_done.notify_all();
-                        continue;
-                    }
-                    break;
-                }
+            while (!paused && !ready.empty() && ok.size() < cfg.max_epoch_jobs) {
+                SrvRequest *r = ready.front();
+                const uint64_t add = r->T * r->poly->G * 8 + r->poly->s * 24 + r->T * 1024;
+                if (!make_room(need + add) && !ok.empty()) break;   // run what fits; a lone request always runs
                 need += add;
-                backlog.pop_front();
-                if (r->resident_id) {
-                    Resident &res = store[r->resident_id];
-                    res.refs++;
-                    res.last_use = ++use_clock;
-                    r->used_id = r->resident_id;
-                }
-                take.push_back(r);
+                ready.pop_front();
+                ok.push_back(r);
             }
         }
-        if (take.empty()) return false;
-        const Clock::time_point t_up0 = Clock::now();
-        // Upload new polynomials (outside the lock), several at a time: host
-        // packing dominates an upload, and the host has cores to spare.
-        std::vector<pe_poly *> made(take.size(), nullptr);
-        std::vector<int> made_st(take.size(), PE_OK);
-        std::vector<size_t> todo;
-        for (size_t j = 0; j < take.size(); ++j)
-            if (!take[j]->resident_id) todo.push_back(j);
-        const size_t nthr = std::min<size_t>(todo.size(), 8);
-        auto upload = [&](size_t first) {
-            cudaSetDevice(device);
-            for (size_t t = first; t < todo.size(); t += nthr) {
-                SrvRequest *r = take[todo[t]];
-                if (!(r->desc.flags & PE_FLAG_BORROW)) {
-                    r->desc.coeffs = r->coeffs.data();
-                    r->desc.exps = r->exps.data();
-                }
-                made_st[todo[t]] = create_poly(&r->desc, &made[todo[t]], false);
-                std::vector<uint8_t>().swap(r->exps);
-                std::vector<uint64_t>().swap(r->coeffs);
-            }
-        };
-        if (nthr <= 1) {
-            if (nthr == 1) upload(0);
-        } else {
-            std::vector<std::thread> th;
-            for (size_t i = 0; i < nthr; ++i) th.emplace_back(upload, i);
-            for (std::thread &x : th) x.join();
-        }
-        std::vector<SrvRequest *> ok;
-        for (size_t j = 0; j < take.size(); ++j) {
-            SrvRequest *r = take[j];
-            if (!r->resident_id) {
-                if (made_st[j] != PE_OK) {
-                    std::vector<SrvRequest *> one{r};
-                    fail(one, made_st[j]);
-                    continue;
-                }
-                pe_poly *P = made[j];
-                std::lock_guard<std::mutex> lk(mu);
-                const uint64_t id = r->reserved_id;
-                Resident res;
-                res.poly = P;
-                res.bytes = P->device_bytes();
-                res.refs = 1;
-                res.last_use = ++use_clock;
-                store[id] = res;
-                resident_bytes += res.bytes;
-                r->poly = P;
-                r->used_id = id;
-            }
-            ok.push_back(r);
-        }
-        t_upload += since(t_up0);
         if (ok.empty()) return false;
         const Clock::time_point t_pl0 = Clock::now();
-        // Outputs, then the batch.
         size_t total = 0;
         for (SrvRequest *r : ok) {
             r->out_bytes = r->T * r->poly->G * 8;
@@ -289,7 +272,7 @@ struct pe_server {
         }
         if (e != cudaSuccess) {
             cuda_fail(e, "server outputs");
-            fail(ok, PE_ERR_NOMEM);
+            fail_all(ok, PE_ERR_NOMEM);
             return true;
         }
         std::vector<pe_job> jobs(ok.size());
@@ -317,7 +300,7 @@ struct pe_server {
         if (st == PE_OK && (e = cudaEventRecord(s.done, s.st)) != cudaSuccess) st = cuda_fail(e, "server event");
         if (st != PE_OK) {
             cudaStreamSynchronize(s.st);
-            fail(ok, st);
+            fail_all(ok, st);
             return true;
         }
         s.reqs = ok;
@@ -348,7 +331,7 @@ struct pe_server {
             std::unique_lock<std::mutex> lk(mu);
             bool any_busy = false;
             for (uint32_t i = 0; i < nslots; ++i) any_busy |= slots[i].busy;
-            if (stop && backlog.empty() && !any_busy) return;
+            if (stop && backlog.empty() && ready.empty() && uploading == 0 && !any_busy) return;
             if (!progressed) {
                 if (any_busy) {
                     lk.unlock();
@@ -388,6 +371,8 @@ extern "C" pe_status poly_eval_server_create(const pe_server_cfg *cfg, pe_server
             return cuda_fail(e, "server streams");
         }
     }
+    const unsigned nup = std::max(1u, std::min(8u, std::thread::hardware_concurrency() / 2));
+    for (unsigned i = 0; i < nup; ++i) S->uploaders.emplace_back([S] { S->upload_loop(); });
     S->worker = std::thread([S] { S->run(); });
     *out = S;
     return PE_OK;
@@ -454,18 +439,9 @@ extern "C" pe_status poly_eval_server_submit(pe_server *S, const pe_request *req
             r->exps.assign(e, e + d.s * d.n * d.exp_bytes);
         }
         n = d.n;
-        uint64_t md = 0, me = 0;   // the groups lie in a (max d + 1) x (max e + 1) grid
-        for (uint64_t i = 0; i < d.s; ++i) {
-            uint64_t x0, x1;
-            if (d.exp_bytes == 1) x0 = e[i * d.n], x1 = e[i * d.n + 1];
-            else if (d.exp_bytes == 2) x0 = ((const uint16_t *)e)[i * d.n], x1 = ((const uint16_t *)e)[i * d.n + 1];
-            else x0 = ((const uint32_t *)e)[i * d.n], x1 = ((const uint32_t *)e)[i * d.n + 1];
-            md = std::max(md, x0);
-            me = std::max(me, x1);
-        }
-        r->g_est = std::min<uint64_t>(d.s, (md + 1) * (me + 1));
-    } else {
-        std::lock_guard<std::mutex> lk(S->mu);
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (req->resident_id) {
         auto it = S->store.find(req->resident_id);
         if (it == S->store.end()) {
             delete r;
@@ -474,32 +450,37 @@ extern "C" pe_status poly_eval_server_submit(pe_server *S, const pe_request *req
         }
         n = it->second.poly->n;
     }
-    if (n > 2) {
-        if (!req->beta) {
-            delete r;
-            set_error("beta is NULL");
-            return PE_ERR_ARG;
-        }
-        r->beta.assign(req->beta, req->beta + (n - 2));
+    if (n > 2 && !req->beta) {
+        delete r;
+        set_error("beta is NULL");
+        return PE_ERR_ARG;
     }
-    r->submitted = Clock::now();
-    std::lock_guard<std::mutex> lk(S->mu);
-    if (S->backlog.size() >= S->cfg.max_queue) {
+    if (S->backlog.size() + S->ready.size() >= S->cfg.max_queue) {
         ++S->rejected;
         delete r;
-        set_error("backlog full");
+        set_error("queue full");
         return PE_ERR_ADMISSION;
     }
+    if (n > 2) r->beta.assign(req->beta, req->beta + (n - 2));
+    r->submitted = Clock::now();
     r->ticket = S->next_ticket++;
-    if (!r->resident_id) {
-        r->reserved_id = S->next_id++;
-        if (req->new_resident_id) *req->new_resident_id = r->reserved_id;
-    }
     S->status[r->ticket] = PE_PENDING;
-    S->backlog.push_back(r);
     ++S->submitted;
     *ticket = r->ticket;
-    S->cv_work.notify_one();
+    if (req->resident_id) {
+        Resident &res = S->store[req->resident_id];
+        res.refs++;                         // keeps it resident until this request completes
+        res.last_use = ++S->use_clock;
+        r->poly = res.poly;
+        r->used_id = req->resident_id;
+        S->ready.push_back(r);
+        S->cv_work.notify_one();
+    } else {
+        r->reserved_id = S->next_id++;
+        if (req->new_resident_id) *req->new_resident_id = r->reserved_id;
+        S->backlog.push_back(r);
+        S->cv_upload.notify_one();
+    }
     return PE_OK;
 }
 
@@ -540,11 +521,11 @@ extern "C" pe_status poly_eval_server_stats(pe_server *S, pe_server_stats *out)
     out->rejected = S->rejected;
     out->epochs = S->epochs;
     out->term_points = S->term_points;
-    out->busy_s = S->busy_s + (S->inflight ? std::chrono::duration<double>(Clock::now() - S->busy_since).count() : 0);
+    out->busy_s = S->busy_s + (S->inflight ? since(S->busy_since) : 0);
     out->resident_bytes = S->resident_bytes;
     out->resident_polys = S->store.size();
     out->evictions = S->evictions;
-    out->upload_s = S->t_upload;   // written by the worker; read without tearing on 64-bit hosts
+    out->upload_s = S->t_upload;
     out->plan_s = S->t_plan;
     out->launch_s = S->t_launch;
     out->finish_s = S->t_finish;
@@ -581,16 +562,20 @@ extern "C" void poly_eval_server_destroy(pe_server *S)
         S->stop = true;
         S->paused = false;
     }
+    S->cv_upload.notify_all();
     S->cv_work.notify_all();
+    for (std::thread &t : S->uploaders)
+        if (t.joinable()) t.join();
     if (S->worker.joinable()) S->worker.join();
+    cudaDeviceSynchronize();
     for (uint32_t i = 0; i < S->nslots; ++i) {
         Slot &s = S->slots[i];
         if (s.staging) cudaFreeHost(s.staging);
         if (s.done) cudaEventDestroy(s.done);
         if (s.st) cudaStreamDestroy(s.st);
     }
-    cudaDeviceSynchronize();
     for (auto &kv : S->store) destroy_idle(kv.second.poly);
     for (SrvRequest *r : S->backlog) delete r;
+    for (SrvRequest *r : S->ready) delete r;
     delete S;
 }
