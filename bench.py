@@ -38,7 +38,8 @@ import workloads as wl  # noqa: E402
 # x*w and q*p, each one wide and two low 32-bit multiplies.  A wide or high
 # multiply occupies the pipe for two slots, a low one for one: 3*2 + 2*2 + 4 = 14.
 # Montgomery: full x*y (4 wide), q = lo*p' (1 wide + 2 low), hi(q*p) (4 wide) = 20.
-SLOTS_PER_TP = {"barrett64": 14, "mont64": 20}
+# 32-bit Barrett (p < 2^30): one high (2 slots) and two low multiplies = 4.
+SLOTS_PER_TP = {"barrett64": 14, "mont64": 20, "barrett32": 4}
 INT_MUL_SLOTS_PER_SM_PER_CLK = 64   # 32-bit integer multiply-add issue rate per SM
 NUM_SMS = 152
 # DRAM bytes (read + write) of one Step B launch on the large workload, from one
@@ -53,7 +54,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large",
-                    choices=["large", "tiny", "width62", "width50", "batched", "served"])
+                    choices=["large", "large30", "tiny", "width62", "width50", "batched", "served"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -69,6 +70,8 @@ def parse():
 def make_workload(name):
     if name == "large":
         return wl.config_large()
+    if name == "large30":
+        return wl.config_large(bits=30)
     if name == "tiny":
         return wl.config_tiny()
     if name == "width62":
@@ -253,7 +256,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     # Roofline of Step B: integer-multiply issue rate at the sampled SM clock.
-    vkey = "mont64" if variant == "mont64" else "barrett64"
+    vkey = variant if variant in SLOTS_PER_TP else ("barrett32" if int(w.p) < (1 << 30) else "barrett64")
     tps_b = s * T / (t_b / runs * 1e-3) if runs and t_b > 0 else None
     mhz = clk["sm_mhz"] or 1920.0
     roof = None

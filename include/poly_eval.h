@@ -64,14 +64,19 @@ typedef enum {
  *       in Montgomery form.  p odd, 3 <= p < 2^62.
  *   PE_MODMUL_FP64: the floating-point FMA product of Algorithm 2 and the
  *       addition of Algorithm 3, in IEEE binary64.  p odd, 3 <= p < 2^50.
- *   PE_MODMUL_AUTO: BARRETT64 (the fastest on this GPU for every width).
+ *   PE_MODMUL_BARRETT32: the fixed-multiplier Barrett product in 32-bit
+ *       words (one high and two low 32-bit multiplies), for the smaller primes
+ *       the paper names as future work (Sect. 6).  p odd, 3 <= p < 2^30.
+ *   PE_MODMUL_AUTO: BARRETT32 when p < 2^30, else BARRETT64 (the fastest on
+ *       this GPU at each width), unless the autotuner has recorded otherwise.
  * All variants give identical, canonical results.
  */
 typedef enum {
     PE_MODMUL_AUTO = 0,
     PE_MODMUL_MONT64 = 1,
     PE_MODMUL_FP64 = 2,
-    PE_MODMUL_BARRETT64 = 3
+    PE_MODMUL_BARRETT64 = 3,
+    PE_MODMUL_BARRETT32 = 4
 } pe_variant;
 
 /* pe_poly_desc.flags */

@@ -29,7 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpolyeval.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "poly_eval.h")
 
-VARIANTS = {"auto": 0, "mont64": 1, "fp64": 2, "barrett64": 3}
+VARIANTS = {"auto": 0, "mont64": 1, "fp64": 2, "barrett64": 3, "barrett32": 4}
 STATUS = {0: "PE_OK", 1: "PE_ERR_ARG", 2: "PE_ERR_PRIME", 3: "PE_ERR_NOT_REDUCED", 4: "PE_ERR_EXP_RANGE",
           5: "PE_ERR_NOMEM", 6: "PE_ERR_ADMISSION", 7: "PE_ERR_CUDA", 8: "PE_ERR_TIMEOUT", 9: "PE_PENDING",
           10: "PE_ERR_NOT_FOUND"}

@@ -414,6 +414,10 @@ static pe_status check_prime(uint64_t p, int variant)
         set_error("the FP64 modular product (Algorithm 2) needs p < 2^50");
         return PE_ERR_PRIME;
     }
+    if (variant == PE_MODMUL_BARRETT32 && p >= (1ull << 30)) {
+        set_error("the 32-bit Barrett product needs p < 2^30");
+        return PE_ERR_PRIME;
+    }
     return PE_OK;
 }
 
@@ -454,7 +458,7 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
     }
     int variant = d->variant;
     if (variant != PE_MODMUL_AUTO && variant != PE_MODMUL_MONT64 && variant != PE_MODMUL_FP64 &&
-        variant != PE_MODMUL_BARRETT64) {
+        variant != PE_MODMUL_BARRETT64 && variant != PE_MODMUL_BARRETT32) {
         set_error("unknown variant %d", (int)d->variant);
         return PE_ERR_ARG;
     }
@@ -546,7 +550,7 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
     P->E = E;
     P->s = s;
     P->requested_variant = variant;
-    P->variant = variant == PE_MODMUL_AUTO ? PE_MODMUL_BARRETT64 : variant;
+    P->variant = variant == PE_MODMUL_AUTO ? default_variant(d->p) : variant;
     P->mc = make_modctx(d->p);
     P->dmax = dmax;
     P->exp_bytes = dmax <= 0xff ? 1 : 2;

@@ -73,19 +73,23 @@ __global__ void __launch_bounds__(128) k_stepB_queue(const StepBJob *__restrict_
             __syncwarp();
         }
         const StepBJob &J = qs.job;
-        switch (J.K * 4 + J.var) {
-        case 1 * 4 + VAR_BARRETT: queue_item<1, VAR_BARRETT>(J, it.y, qs.w); break;
-        case 2 * 4 + VAR_BARRETT: queue_item<2, VAR_BARRETT>(J, it.y, qs.w); break;
-        case 4 * 4 + VAR_BARRETT: queue_item<4, VAR_BARRETT>(J, it.y, qs.w); break;
-        case 8 * 4 + VAR_BARRETT: queue_item<8, VAR_BARRETT>(J, it.y, qs.w); break;
-        case 1 * 4 + VAR_MONT: queue_item<1, VAR_MONT>(J, it.y, qs.w); break;
-        case 2 * 4 + VAR_MONT: queue_item<2, VAR_MONT>(J, it.y, qs.w); break;
-        case 4 * 4 + VAR_MONT: queue_item<4, VAR_MONT>(J, it.y, qs.w); break;
-        case 8 * 4 + VAR_MONT: queue_item<8, VAR_MONT>(J, it.y, qs.w); break;
-        case 1 * 4 + VAR_FP64: queue_item<1, VAR_FP64>(J, it.y, qs.w); break;
-        case 2 * 4 + VAR_FP64: queue_item<2, VAR_FP64>(J, it.y, qs.w); break;
-        case 4 * 4 + VAR_FP64: queue_item<4, VAR_FP64>(J, it.y, qs.w); break;
-        case 8 * 4 + VAR_FP64: queue_item<8, VAR_FP64>(J, it.y, qs.w); break;
+        switch (J.K * 8 + J.var) {
+        case 1 * 8 + VAR_BARRETT: queue_item<1, VAR_BARRETT>(J, it.y, qs.w); break;
+        case 2 * 8 + VAR_BARRETT: queue_item<2, VAR_BARRETT>(J, it.y, qs.w); break;
+        case 4 * 8 + VAR_BARRETT: queue_item<4, VAR_BARRETT>(J, it.y, qs.w); break;
+        case 8 * 8 + VAR_BARRETT: queue_item<8, VAR_BARRETT>(J, it.y, qs.w); break;
+        case 1 * 8 + VAR_MONT: queue_item<1, VAR_MONT>(J, it.y, qs.w); break;
+        case 2 * 8 + VAR_MONT: queue_item<2, VAR_MONT>(J, it.y, qs.w); break;
+        case 4 * 8 + VAR_MONT: queue_item<4, VAR_MONT>(J, it.y, qs.w); break;
+        case 8 * 8 + VAR_MONT: queue_item<8, VAR_MONT>(J, it.y, qs.w); break;
+        case 1 * 8 + VAR_FP64: queue_item<1, VAR_FP64>(J, it.y, qs.w); break;
+        case 2 * 8 + VAR_FP64: queue_item<2, VAR_FP64>(J, it.y, qs.w); break;
+        case 4 * 8 + VAR_FP64: queue_item<4, VAR_FP64>(J, it.y, qs.w); break;
+        case 8 * 8 + VAR_FP64: queue_item<8, VAR_FP64>(J, it.y, qs.w); break;
+        case 1 * 8 + VAR_BARRETT32: queue_item<1, VAR_BARRETT32>(J, it.y, qs.w); break;
+        case 2 * 8 + VAR_BARRETT32: queue_item<2, VAR_BARRETT32>(J, it.y, qs.w); break;
+        case 4 * 8 + VAR_BARRETT32: queue_item<4, VAR_BARRETT32>(J, it.y, qs.w); break;
+        case 8 * 8 + VAR_BARRETT32: queue_item<8, VAR_BARRETT32>(J, it.y, qs.w); break;
         default: break;
         }
         __syncwarp();

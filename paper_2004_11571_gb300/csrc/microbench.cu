@@ -93,7 +93,8 @@ extern "C" pe_status poly_eval_modmul_peak(pe_variant variant, uint64_t p, doubl
         set_error("NULL output");
         return PE_ERR_ARG;
     }
-    if (p < 3 || !(p & 1) || p >= (1ull << 62) || (variant == PE_MODMUL_FP64 && p >= (1ull << 50))) {
+    if (p < 3 || !(p & 1) || p >= (1ull << 62) || (variant == PE_MODMUL_FP64 && p >= (1ull << 50)) ||
+        (variant == PE_MODMUL_BARRETT32 && p >= (1ull << 30))) {
         set_error("p out of range for the variant");
         return PE_ERR_PRIME;
     }
@@ -101,6 +102,7 @@ extern "C" pe_status poly_eval_modmul_peak(pe_variant variant, uint64_t p, doubl
     switch (variant) {
     case PE_MODMUL_MONT64: return run_peak<VAR_MONT>(mc, tps, mhz);
     case PE_MODMUL_FP64: return run_peak<VAR_FP64>(mc, tps, mhz);
+    case PE_MODMUL_BARRETT32: return run_peak<VAR_BARRETT32>(mc, tps, mhz);
     case PE_MODMUL_AUTO:
     case PE_MODMUL_BARRETT64: return run_peak<VAR_BARRETT>(mc, tps, mhz);
     default: set_error("unknown variant"); return PE_ERR_ARG;

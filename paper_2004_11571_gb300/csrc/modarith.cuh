@@ -63,6 +63,13 @@ __device__ __forceinline__ uint64_t barrett_mul_lazy4(uint64_t x, uint64_t w, ui
     return x * w - q * p;
 }
 
+// 32-bit words, p < 2^30: with wq = floor(w * 2^32 / p) and any x < 2^32,
+// x*w - hi(x*wq)*p lies in [0, 2p) (same argument as above, one word).
+__device__ __forceinline__ uint32_t barrett_mul32(uint32_t x, uint32_t w, uint32_t wq, uint32_t p)
+{
+    return x * w - __umulhi(x, wq) * p;
+}
+
 // Given mR = m * 2^64 mod p (canonical), the Barrett quotient of m is
 // (m*2^64 - mR) / p, an exact division, hence equal to -mR * p^-1 mod 2^64.
 __device__ __forceinline__ uint64_t barrett_quotient_from_mont(uint64_t mR, const ModCtx &mc)

@@ -153,6 +153,7 @@ static cudaError_t dispatch(int K, int var, const StepBJob &J, uint32_t n0, cons
     case VAR_BARRETT: return dispatch_k<VAR_BARRETT>(K, J, n0, J1, n1, wpb, st, occ);
     case VAR_MONT: return dispatch_k<VAR_MONT>(K, J, n0, J1, n1, wpb, st, occ);
     case VAR_FP64: return dispatch_k<VAR_FP64>(K, J, n0, J1, n1, wpb, st, occ);
+    case VAR_BARRETT32: return dispatch_k<VAR_BARRETT32>(K, J, n0, J1, n1, wpb, st, occ);
     default: return cudaErrorInvalidValue;
     }
 }

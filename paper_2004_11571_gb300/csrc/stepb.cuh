@@ -31,7 +31,7 @@
 
 namespace pe {
 
-enum : int { VAR_MONT = 1, VAR_FP64 = 2, VAR_BARRETT = 3 };
+enum : int { VAR_MONT = 1, VAR_FP64 = 2, VAR_BARRETT = 3, VAR_BARRETT32 = 4 };
 
 constexpr int kWalkStride = 33;  // shared-memory row stride (conflict-free transpose)
 
@@ -52,6 +52,20 @@ struct Lane<VAR_BARRETT> {
         v = v0;
         w = canon(mont_redc(mR, 0, mc), mc.p);
         wq = barrett_quotient_from_mont(mR, mc);
+    }
+    __device__ __forceinline__ void zero() { v = 0; w = 0; wq = 0; }
+};
+
+// 32-bit lanes (p < 2^30): floor(m * 2^32 / p) is the top word of the 64-bit
+// quotient floor(m * 2^64 / p).
+template <>
+struct Lane<VAR_BARRETT32> {
+    uint32_t v, w, wq;
+    __device__ __forceinline__ void init(uint64_t v0, uint64_t mR, const ModCtx &mc)
+    {
+        v = (uint32_t)v0;
+        w = (uint32_t)canon(mont_redc(mR, 0, mc), mc.p);
+        wq = (uint32_t)(barrett_quotient_from_mont(mR, mc) >> 32);
     }
     __device__ __forceinline__ void zero() { v = 0; w = 0; wq = 0; }
 };
@@ -89,6 +103,16 @@ __device__ __forceinline__ void lane_point(Lane<VAR> (&st)[K], const ModCtx &mc,
         }
         lo = (uint64_t)acc;
         hi = 0;
+    } else if constexpr (VAR == VAR_BARRETT32) {
+        // K values below 2^32 each: the sum fits in 64 bits.
+        const uint32_t p = (uint32_t)mc.p;
+        lo = 0;
+        hi = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            lo += st[k].v;
+            st[k].v = barrett_mul32(st[k].v, st[k].w, st[k].wq, p);
+        }
     } else {
         lo = 0;
         hi = 0;

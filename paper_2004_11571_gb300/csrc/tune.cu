@@ -24,7 +24,8 @@ static int lg(double x) { return (int)std::lround(std::log2(std::max(1.0, x))); 
 std::string tune_key(const pe_poly *P, uint64_t T)
 {
     char buf[96];
-    snprintf(buf, sizeof buf, "p%d|s%d|T%d|gs%d", P->p < (1ull << 50) ? 50 : 62, lg((double)P->s), lg((double)T),
+    snprintf(buf, sizeof buf, "p%d|s%d|T%d|gs%d", P->p < (1ull << 30) ? 30 : P->p < (1ull << 50) ? 50 : 62,
+             lg((double)P->s), lg((double)T),
              lg((double)P->s / (double)std::max<uint64_t>(1, P->G)));
     return buf;
 }
@@ -36,11 +37,13 @@ const TuneEntry *tune_lookup(const pe_poly *P, uint64_t T)
     return it == g_tune.end() ? nullptr : &it->second;
 }
 
+int default_variant(uint64_t p) { return p < (1ull << 30) ? PE_MODMUL_BARRETT32 : PE_MODMUL_BARRETT64; }
+
 int run_variant(pe_poly *P, uint64_t T)
 {
     if (P->requested_variant != PE_MODMUL_AUTO) return P->requested_variant;
     const TuneEntry *te = tune_lookup(P, T);
-    return te ? te->variant : PE_MODMUL_BARRETT64;
+    return te ? te->variant : default_variant(P->p);
 }
 
 }  // namespace pe
@@ -71,6 +74,7 @@ extern "C" pe_status poly_eval_tune(pe_poly *P, uint64_t T, pe_tiles *best, doub
     const int saved_req = P->requested_variant;
     std::vector<int> variants = {PE_MODMUL_BARRETT64, PE_MODMUL_MONT64};
     if (P->p < (1ull << 50)) variants.push_back(PE_MODMUL_FP64);
+    if (P->p < (1ull << 30)) variants.push_back(PE_MODMUL_BARRETT32);
     if (saved_req != PE_MODMUL_AUTO) variants = {saved_req};
     TuneEntry bestE;
     bestE.ms = 1e300;
@@ -178,7 +182,7 @@ extern "C" pe_status poly_eval_tune_load(const char *path)
         if (r == std::string::npos ||
             sscanf(line.c_str() + r, "\"K\": %u, \"wpb\": %u, \"variant\": %d, \"ms\": %lf", &K, &w, &v, &ms) != 4)
             continue;
-        if ((K != 1 && K != 2 && K != 4 && K != 8 && K != 16) || w < 1 || w > 8 || v < 1 || v > 3) continue;
+        if ((K != 1 && K != 2 && K != 4 && K != 8 && K != 16) || w < 1 || w > 8 || v < 1 || v > 4) continue;
         t.K = K;
         t.wpb = w;
         t.variant = v;

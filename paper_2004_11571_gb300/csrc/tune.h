@@ -14,5 +14,6 @@ struct TuneEntry {
 std::string tune_key(const pe_poly *P, uint64_t T);
 const TuneEntry *tune_lookup(const pe_poly *P, uint64_t T);   // nullptr when untuned
 int run_variant(pe_poly *P, uint64_t T);                       // modular product for a plain run
+int default_variant(uint64_t p);                               // fastest product for the prime's width
 
 }  // namespace pe

@@ -67,6 +67,25 @@ def test_batch_matches_oracle_and_plain():
     batch.close()
 
 
+def test_batch_with_30_bit_primes():
+    p30 = wl.random_prime(30, 91)
+    ws = [wl.make_zipf(n=6 + k % 4, s=5_000 + 3_000 * k, p=p30, deg12=10 + k, deg_rest=8, T=60 + 20 * k, seed=k)
+          for k in range(6)]
+    jobs, outs = [], []
+    for k, w in enumerate(ws):
+        poly = pe.Poly.from_workload(w, variant="barrett64" if k == 5 else "auto")
+        out = torch.full((w.T, poly.G), -1, dtype=torch.int64, device="cuda")
+        jobs.append((poly, w.beta, w.T, 2, out))
+        outs.append(out)
+    batch = pe.Batch(jobs)
+    batch.launch()
+    torch.cuda.synchronize()
+    for w, o in zip(ws, outs):
+        _, ref = oracle.eval_direct(w, t0=2)
+        assert np.array_equal(pe.to_u64(o), ref)
+    batch.close()
+
+
 def test_batch_edge_jobs():
     p = wl.random_prime(62, 88)
     ws = [wl.make_uniform(n=6, s=1, p=p, deg12=2, deg_rest=3, T=3, seed=1),

@@ -22,6 +22,7 @@ import paper_2004_11571_gb300 as pe  # noqa: E402
 
 P62 = wl.random_prime(62, 21)
 P50 = wl.random_prime(50, 22)
+P30 = wl.random_prime(30, 24)
 
 
 def _gpu(w, variant="auto", tiles=None, T=None, t0=None):
@@ -67,6 +68,22 @@ def test_fp64_variant(K):
     _check_full(w, "fp64", dict(K=K, slabs=2, tchunk=45))
     _check_full(w, "fp64")
     _check_full(w, "barrett64")
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8, 16])
+def test_barrett32_variant(K):
+    # primes below 2^30 run the 32-bit product (the default for them)
+    w = wl.make_zipf(n=7, s=25_000, p=P30, deg12=18, deg_rest=9, T=90, seed=25)
+    _check_full(w, "barrett32", dict(K=K, slabs=2, tchunk=40))
+    if K == 8:
+        _check_full(w)
+        _check_full(w, "barrett32", None, t0=0)
+        _check_full(wl.make_uniform(n=6, s=3_000, p=(1 << 30) - 35, deg12=8, deg_rest=5, T=70, seed=26), "barrett32")
+        poly = pe.Poly.from_workload(w)
+        assert poly.plan_info(w.T)["variant"] == 4
+        poly.close()
+        with pytest.raises(pe.PolyEvalError):
+            pe.Poly.from_workload(wl.config_tiny(), variant="barrett32")     # 62-bit prime
 
 
 def test_automatic_tiles_and_ragged_sizes():

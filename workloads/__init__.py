@@ -197,12 +197,12 @@ def config_tiny(seed: int = SEED_TINY) -> Workload:
                         name="tiny n=6 s=2000 T=64 p62")
 
 
-def config_large(seed: int = SEED_LARGE, s: int = 1_000_000, T: int = 1024) -> Workload:
-    """n=9, 62-bit p, 1e6 terms, 71x71 (x1,x2) cells with Zipf(1.1) group sizes,
-    x3..x9 in 0..20, T=1024."""
-    p = random_prime(62, seed)
+def config_large(seed: int = SEED_LARGE, s: int = 1_000_000, T: int = 1024, bits: int = 62) -> Workload:
+    """n=9, 62-bit p (or `bits`), 1e6 terms, 71x71 (x1,x2) cells with Zipf(1.1)
+    group sizes, x3..x9 in 0..20, T=1024."""
+    p = random_prime(bits, seed if bits == 62 else seed + bits)
     return make_zipf(n=9, s=s, p=p, deg12=70, deg_rest=20, T=T, seed=seed + 1, a=1.1,
-                     name=f"large n=9 s={s} G=5041 zipf1.1 T={T} p62")
+                     name=f"large n=9 s={s} G=5041 zipf1.1 T={T} p{bits}")
 
 
 def config_width(bits: int, seed: int = SEED_WIDTH, s: int = 4_000_000, T: int = 4096) -> Workload:
