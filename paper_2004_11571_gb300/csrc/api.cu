@@ -201,11 +201,15 @@ Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
         t.K = te->K;
     } else {
         // Padded slots plus the per-chunk walk: a chunk costs K products+sums
-        // and one walk entry (~0.7 of a product+sum) per point.
+        // and one walk entry per point.  A walk entry costs ~0.7 of a 64-bit
+        // product+sum and ~2.4 of a 32-bit one, so 32-bit products also try K=16.
+        const bool narrow = P->variant == PE_MODMUL_BARRETT32;
+        const double walk = narrow ? 2.4 : 0.7;
         double best = 1e300;
-        for (uint32_t K : {1u, 2u, 4u, 8u}) {
+        for (uint32_t K : {1u, 2u, 4u, 8u, 16u}) {
+            if (K == 16 && !narrow) break;
             const double nc = (double)count_chunks(P, K);
-            const double c = nc * (K + 0.7);
+            const double c = nc * (K + walk);
             if (c < best * 0.98) {
                 best = c;
                 t.K = K;
