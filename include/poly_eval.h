@@ -162,7 +162,7 @@ typedef struct {
     uint32_t K;               /* terms per lane: 1, 2, 4, 8 or 16 */
     uint32_t slabs;           /* slabs per work item */
     uint32_t tchunk;          /* points per work item */
-    uint32_t warps_per_block; /* 1..8 */
+    uint32_t warps_per_block; /* 1..8 (the plain Step B kernel uses at most 4) */
     uint32_t tail;            /* with slabs and tchunk forced: final points run as a band of
                                  one-slab items issued after the others (0: none) */
 } pe_tiles;

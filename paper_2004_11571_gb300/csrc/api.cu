@@ -195,6 +195,7 @@ Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
     Tiles t;
     const TuneEntry *te = tune_lookup(P, T);
     t.wpb = (f && f->warps_per_block) ? f->warps_per_block : (te ? te->wpb : 4);
+    t.wpb = std::min<uint32_t>(t.wpb, kMaxStepBWarps);
     if (f && f->K) {
         t.K = f->K;
     } else if (te) {

@@ -5,6 +5,8 @@
 
 namespace pe {
 
+constexpr int kMaxStepBWarps = 4;   // warps per block of the plain Step B kernel
+
 cudaError_t launch_powtab(const BetaArg &beta, uint32_t E, uint32_t dp1, const ModCtx &mc, uint64_t *ptab,
                           cudaStream_t st);
 cudaError_t launch_stepA(const void *exps, uint32_t exp_bytes, uint64_t s, uint32_t E, const uint64_t *ptab,

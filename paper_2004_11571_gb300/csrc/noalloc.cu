@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kNaWarps * 32) k_stepB_noalloc(NoAllocJob J)
                 uint32_t hi;
                 lane_point<1, VAR_BARRETT>(st, mc, lo, hi);
                 sm.lo[tt * kWalkStride + lane] = lo;
-                sm.hi[tt * kWalkStride + lane] = hi;
+                sm.hi[tt * kWalkStride + lane] = (uint8_t)hi;
             }
             __syncwarp();
             if ((uint32_t)lane < nt) {

@@ -61,8 +61,10 @@ __global__ void k_stepA_starts(const ExpT *__restrict__ exps, const uint64_t *__
 // Two bands of work items: J0 covers the first rows with large items, J1 the
 // last rows with small ones.  Blocks are issued in index order, so the small
 // items run last and fill the SMs that finish their large items early.
+// At most 4 warps per block, 5 blocks per SM: 20 warps fit the register file
+// (<= 96 registers) and shared memory (9.6 KB per warp).
 template <int K, int VAR>
-__global__ void __launch_bounds__(256) k_stepB(StepBJob J0, uint32_t n0, StepBJob J1, uint32_t n1)
+__global__ void __launch_bounds__(128, 5) k_stepB(StepBJob J0, uint32_t n0, StepBJob J1, uint32_t n1)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *sm = reinterpret_cast<WarpSmem *>(smem_raw);
@@ -120,7 +122,7 @@ static cudaError_t launch_b(const StepBJob &J, uint32_t nitems, const StepBJob &
     static bool attr_set = false;   // once, at the largest block (8 warps)
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_stepB<K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(8 * sizeof(WarpSmem)));
+                                             (int)(kMaxStepBWarps * sizeof(WarpSmem)));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -148,7 +150,7 @@ static cudaError_t dispatch_k(int K, const StepBJob &J, uint32_t n0, const StepB
 static cudaError_t dispatch(int K, int var, const StepBJob &J, uint32_t n0, const StepBJob &J1, uint32_t n1, int wpb,
                             cudaStream_t st, int *occ)
 {
-    if (wpb < 1 || wpb > 8) return cudaErrorInvalidValue;
+    if (wpb < 1 || wpb > kMaxStepBWarps) return cudaErrorInvalidValue;
     switch (var) {
     case VAR_BARRETT: return dispatch_k<VAR_BARRETT>(K, J, n0, J1, n1, wpb, st, occ);
     case VAR_MONT: return dispatch_k<VAR_MONT>(K, J, n0, J1, n1, wpb, st, occ);

@@ -35,10 +35,13 @@ enum : int { VAR_MONT = 1, VAR_FP64 = 2, VAR_BARRETT = 3, VAR_BARRETT32 = 4 };
 
 constexpr int kWalkStride = 33;  // shared-memory row stride (conflict-free transpose)
 
+// Per-warp transpose buffer.  The high word of a lane partial (K values below
+// 2^64 each, K <= 16) is below 16, so it is kept in a byte.
 struct WarpSmem {
     uint64_t lo[32 * kWalkStride];
-    uint32_t hi[32 * kWalkStride];
     uint32_t g[32];
+    uint8_t hi[32 * kWalkStride];
+    uint8_t pad[(16 - (32 * kWalkStride) % 16) % 16];
 };
 
 template <int VAR>
@@ -224,7 +227,7 @@ __device__ __forceinline__ void stepb_item(const StepBJob &J, uint32_t item, War
                 uint32_t hi;
                 lane_point<K, VAR>(st, mc, lo, hi);
                 sm.lo[tt * kWalkStride + lane] = lo;
-                sm.hi[tt * kWalkStride + lane] = hi;
+                sm.hi[tt * kWalkStride + lane] = (uint8_t)hi;
             }
             __syncwarp();
             if ((uint32_t)lane < nt) {
@@ -233,7 +236,7 @@ __device__ __forceinline__ void stepb_item(const StepBJob &J, uint32_t item, War
                 uint32_t ahi = (uint32_t)cin.y;
                 bool first = slab_first;
                 const uint64_t *plo = sm.lo + lane * kWalkStride;
-                const uint32_t *phi = sm.hi + lane * kWalkStride;
+                const uint8_t *phi = sm.hi + lane * kWalkStride;
                 for (uint32_t l = 0; l < nvalid; ++l) {
                     if ((bmask >> l) & 1u) {
                         close_group(J, row, sm.g[l - 1], first, false, lslot, rslot, alo, ahi);
