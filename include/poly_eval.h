@@ -138,8 +138,11 @@ pe_status poly_eval_groups(const pe_poly *poly, uint64_t *G, uint32_t *keys);
  *          copies the result back and returns after the stream has finished.
  * Runs Step A (power tables, monomial values) and Step B (Hadamard products
  * and coefficient reductions) as CUDA kernels.  Scratch device memory is owned
- * by the handle and reused by later calls; calls on one handle must not
- * overlap in time.
+ * by the handle and reused by later calls, so runs of one handle execute one
+ * after another on the device even when issued on different streams (each
+ * run's stream waits for the previous run); use separate handles for
+ * concurrent evaluations.  The host-side call itself is not thread-safe per
+ * handle.
  */
 pe_status poly_eval_run(pe_poly *poly, const uint64_t *beta, uint64_t T, uint64_t t0,
                         uint64_t *out, void *stream);

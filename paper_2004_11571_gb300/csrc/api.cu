@@ -773,9 +773,13 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
         return PE_ERR_ARG;
     }
     cudaStream_t cs = (cudaStream_t)stream;
-    // Buffers replaced below (plans, start values, output scratch) are freed on
-    // the allocation stream only after the previous run has finished with them.
-    if (P->last_use) cudaStreamWaitEvent(alloc_stream(), P->last_use, 0);
+    // Runs of one handle share its scratch (power tables, monomials, starting
+    // values, plans), so a run on any stream starts after the previous one has
+    // finished; buffers replaced below are freed only after that run as well.
+    if (P->last_use) {
+        cudaStreamWaitEvent(cs, P->last_use, 0);
+        cudaStreamWaitEvent(alloc_stream(), P->last_use, 0);
+    }
     Tiles t;
     if ((st = plan_for(P, T, &t)) != PE_OK) return st;
     cudaPointerAttributes attr{};

@@ -226,8 +226,9 @@ def test_full_size_configs_sampled(name):
 
 
 def test_replanning_while_previous_run_is_in_flight():
-    # Runs with different T on two streams re-plan the handle; buffers of the
-    # earlier, still-running launch must not be reused under it.
+    # Runs with different T on two streams re-plan the handle and share its
+    # scratch: each run must wait for the previous one, and buffers of an
+    # earlier launch must not be reused under it.
     w = wl.make_zipf(n=7, s=200_000, p=P62, deg12=30, deg_rest=9, T=700, seed=23)
     cells = oracle.CellOracle(w)
     poly = pe.Poly.from_workload(w)
