@@ -33,14 +33,16 @@ import numpy as np  # noqa: E402
 
 import workloads as wl  # noqa: E402
 
-# Integer-multiply pipe issue slots per term-point of the modular product.
-# Lazy Barrett: quotient x1*w1 (wide) + hi(x1*w0) + hi(x0*w1); low products
-# x*w and q*p, each one wide and two low 32-bit multiplies.  A wide or high
-# multiply occupies the pipe for two slots, a low one for one: 3*2 + 2*2 + 4 = 14.
-# Montgomery: full x*y (4 wide), q = lo*p' (1 wide + 2 low), hi(q*p) (4 wide) = 20.
-# 32-bit Barrett (p < 2^30): one high (2 slots) and two low multiplies = 4.
-SLOTS_PER_TP = {"barrett64": 14, "mont64": 20, "barrett32": 4}
-INT_MUL_SLOTS_PER_SM_PER_CLK = 64   # 32-bit integer multiply-add issue rate per SM
+# 32-bit integer operations per term-point of each modular product, by kind.
+# Lazy Barrett: quotient x1*w1 (wide) + hi(x1*w0) + hi(x0*w1); the low halves of
+# x*w and q*p, each one wide and two low multiplies.  Montgomery: the 128-bit
+# x*y and hi(q*p) (each one high and three wide), q = lo*p' (one wide, two low).
+# 32-bit Barrett: hi(x*wq) and two low multiplies.  The roofline weights each
+# kind by the measured issue rate of mad.lo relative to its own
+# (poly_eval_int_pipe_rates), so `peak` is the mad.lo rate of all SMs at the
+# sampled clock and `achieved` is Step B's term-points/s times the weighted count.
+OPS_PER_TP = {"barrett64": {"wide": 3, "hi": 2, "lo": 4}, "mont64": {"wide": 8, "hi": 2, "lo": 4},
+              "barrett32": {"wide": 0, "hi": 1, "lo": 2}}
 NUM_SMS = 152
 # DRAM bytes (read + write) of one Step B launch on the large workload, from one
 # ncu capture of the current kernel; None for other workloads.
@@ -261,18 +263,24 @@ def run_ours(args):
     mhz = clk["sm_mhz"] or 1920.0
     roof = None
     if variant != "fp64" and tps_b:
-        peak = NUM_SMS * INT_MUL_SLOTS_PER_SM_PER_CLK * mhz * 1e6 / 1e9
-        ach = tps_b * SLOTS_PER_TP[vkey] / 1e9
+        rates = pe.int_pipe_rates()
+        cost = {"lo": 1.0, "hi": rates["mad_lo"] / rates["mad_hi"], "wide": rates["mad_lo"] / rates["mad_wide"]}
+        slots = sum(n * cost[k] for k, n in OPS_PER_TP[vkey].items())
+        peak = NUM_SMS * rates["mad_lo"] * mhz * 1e6 / 1e9
+        ach = tps_b * slots / 1e9
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gslot/s", "frac": ach / peak,
                 "traffic": STEPB_TRAFFIC_LARGE if args.config == "large" and vkey == "barrett64" else None,
                 "kernel": "pe::k_stepB",
-                "peak_source": f"{NUM_SMS} SMs x {INT_MUL_SLOTS_PER_SM_PER_CLK} integer-multiply issue slots/clk x "
+                "peak_source": f"{NUM_SMS} SMs x {rates['mad_lo']:.1f} mad.lo.u32 per SM-clock (measured) x "
                                f"{mhz:.0f} MHz (median sampled SM clock)",
-                "algorithmic": f"{SLOTS_PER_TP[vkey]} multiply-pipe slots per term-point x {s}x{T} term-points",
+                "algorithmic": f"{OPS_PER_TP[vkey]} 32-bit operations per term-point = {slots:.2f} mad.lo slots "
+                               f"(measured per-SM-clock rates {rates}) x {s}x{T} term-points",
+                "peak_term_points_per_s": peak * 1e9 / slots,
                 "stepB_ms": t_b / runs, "stepB_term_points_per_s": tps_b}
         try:
             cal, cal_mhz = pe.modmul_peak(vkey, w.p)
             roof["calibration"] = {"register_only_term_points_per_s": cal, "frac_of_register_only": tps_b / cal,
+                                   "register_only_frac_of_peak": cal * slots / (peak * 1e9),
                                    "sm_mhz_in_kernel": cal_mhz}
         except Exception as ex:  # pragma: no cover
             roof["calibration"] = {"error": str(ex)}

@@ -333,6 +333,14 @@ void poly_eval_server_destroy(pe_server *srv);
 pe_status poly_eval_modmul_peak(pe_variant variant, uint64_t p, double *term_points_per_s,
                                 double *sm_clock_mhz);
 
+/*
+ * Measured issue rates of single 32-bit integer instructions, in thread
+ * operations per SM per clock, from independent dependency chains at full
+ * occupancy: rates[0] mad.lo.u32, rates[1] mad.hi.u32, rates[2] mad.wide.u32,
+ * rates[3] add.u32.  They are the unit counts behind the integer roofline.
+ */
+pe_status poly_eval_int_pipe_rates(double rates[4]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -136,6 +136,7 @@ def lib():
             "poly_eval_server_pause": (st, [_vp, ctypes.c_int]),
             "poly_eval_modmul_peak": (st, [ctypes.c_int, _u64, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]),
+            "poly_eval_int_pipe_rates": (st, [ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -424,6 +425,13 @@ def modmul_peak(variant="barrett64", p: int = (1 << 61) - 1):
     tps, mhz = ctypes.c_double(), ctypes.c_double()
     _check(lib().poly_eval_modmul_peak(_variant(variant), int(p), ctypes.byref(tps), ctypes.byref(mhz)))
     return tps.value, mhz.value
+
+
+def int_pipe_rates() -> dict:
+    """Thread operations per SM per clock of mad.lo / mad.hi / mad.wide / add (u32)."""
+    r = (ctypes.c_double * 4)()
+    _check(lib().poly_eval_int_pipe_rates(r))
+    return {"mad_lo": r[0], "mad_hi": r[1], "mad_wide": r[2], "add": r[3]}
 
 
 def to_u64(t) -> np.ndarray:

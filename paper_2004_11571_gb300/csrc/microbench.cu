@@ -83,9 +83,102 @@ static pe_status run_peak(const ModCtx &mc, double *tps, double *mhz)
     return PE_OK;
 }
 
+// Integer pipe rates: 8 independent dependency chains per thread of one
+// instruction kind (PTX mad.lo.u32, mad.hi.u32, mad.wide.u32, add.u32).
+template <int KIND>
+__global__ void __launch_bounds__(256) k_int_rate(uint32_t *sink, uint32_t iters, unsigned long long *clk)
+{
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t x[8];
+    uint64_t w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        x[k] = tid * 2654435761u + k * 40503u + 1u;
+        w[k] = x[k];
+    }
+    const uint32_t y = 0x9E3779B1u ^ (tid >> 5), c = 12345u + (tid & 7);
+    unsigned long long c0 = 0, g0 = 0;
+    if (tid == 0) {
+        c0 = clock64();
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g0));
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if constexpr (KIND == 0) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[k]) : "r"(y), "r"(c));
+                if constexpr (KIND == 1) asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(x[k]) : "r"(y), "r"(c));
+                if constexpr (KIND == 2) {
+                    asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[k]) : "r"((uint32_t)w[k]), "r"(y));
+                }
+                if constexpr (KIND == 3) asm volatile("add.u32 %0, %0, %1;" : "+r"(x[k]) : "r"(y));
+            }
+        }
+    }
+    if (tid == 0) {
+        unsigned long long g1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g1));
+        clk[0] = clock64() - c0;
+        clk[1] = g1 - g0;
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc ^= x[k] ^ (uint32_t)w[k] ^ (uint32_t)(w[k] >> 32);
+    sink[tid] = acc;
+}
+
+template <int KIND>
+static pe_status int_rate(double *per_sm_clk)
+{
+    int bps = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_int_rate<KIND>, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    bps = std::max(1, bps);
+    const uint32_t grid = (uint32_t)(bps * num_sms());
+    const uint64_t threads = (uint64_t)grid * 256;
+    DevBuf sink, clk;
+    if ((e = sink.ensure(threads * 4)) != cudaSuccess || (e = clk.ensure(16)) != cudaSuccess)
+        return cuda_fail(e, "alloc");
+    const uint32_t iters = 1u << 14;
+    k_int_rate<KIND><<<grid, 256>>>(sink.as<uint32_t>(), iters / 16, clk.as<unsigned long long>());  // warm-up
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a);
+    k_int_rate<KIND><<<grid, 256>>>(sink.as<uint32_t>(), iters, clk.as<unsigned long long>());
+    cudaEventRecord(b);
+    unsigned long long hc[2] = {0, 0};
+    float ms = 0.f;
+    if ((e = cudaEventSynchronize(b)) == cudaSuccess && (e = cudaGetLastError()) == cudaSuccess)
+        e = cudaMemcpy(hc, clk.p, 16, cudaMemcpyDeviceToHost);
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_fail(e, "int rate");
+    // Kernel time from events; the SM clock from thread 0's cycle and nanosecond
+    // counters (warps are not scheduled evenly, so its cycle count is not the duration).
+    const double hz = hc[1] ? (double)hc[0] / (double)hc[1] * 1e9 : 1.9e9;
+    *per_sm_clk = (double)threads * iters * 32.0 / ((double)num_sms() * (ms * 1e-3) * hz);
+    return PE_OK;
+}
+
 }  // namespace pe
 
 using namespace pe;
+
+extern "C" pe_status poly_eval_int_pipe_rates(double rates[4])
+{
+    if (!rates) {
+        set_error("NULL output");
+        return PE_ERR_ARG;
+    }
+    pe_status st;
+    if ((st = int_rate<0>(&rates[0])) != PE_OK || (st = int_rate<1>(&rates[1])) != PE_OK ||
+        (st = int_rate<2>(&rates[2])) != PE_OK || (st = int_rate<3>(&rates[3])) != PE_OK)
+        return st;
+    return PE_OK;
+}
 
 extern "C" pe_status poly_eval_modmul_peak(pe_variant variant, uint64_t p, double *tps, double *mhz)
 {
