@@ -258,7 +258,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     # Roofline of Step B: integer-multiply issue rate at the sampled SM clock.
-    vkey = variant if variant in SLOTS_PER_TP else ("barrett32" if int(w.p) < (1 << 30) else "barrett64")
+    vkey = variant if variant in OPS_PER_TP else ("barrett32" if int(w.p) < (1 << 30) else "barrett64")
     tps_b = s * T / (t_b / runs * 1e-3) if runs and t_b > 0 else None
     mhz = clk["sm_mhz"] or 1920.0
     roof = None
