@@ -158,6 +158,35 @@ def cpu_baseline(w, stride):
             "seconds": dt}
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this machine's GPUs, else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def bench_compact(pe, dense, torch, reps=20):
+    """Sparse images of the benchmark's output (poly_eval_compact): one read of
+    the dense images to count, one to write, 12 bytes per kept coefficient."""
+    T, G = dense.shape
+    for _ in range(3):
+        pe.compact(dense)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        row_ptr, cols, vals = pe.compact(dense)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / reps
+    nnz = int(cols.shape[0])
+    algo = 2 * T * G * 8 + 12 * nnz + 8 * (T + 1)
+    peak, src = hbm_peak_gbs()
+    return {"nnz": nnz, "ms": dt * 1e3, "bound": "hbm", "achieved_gbs": algo / dt / 1e9, "peak_gbs": peak,
+            "frac": algo / dt / 1e9 / peak, "peak_source": src,
+            "note": "host-timed, includes one stream synchronization per call"}
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -302,6 +331,8 @@ def run_ours(args):
             "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_stride)
+    if world == 1 and not args.no_extras:
+        line["sparse_images"] = bench_compact(pe, out, torch)
     poly.close()
     if world == 1 and not args.no_extras:
         del out, flush

@@ -200,6 +200,22 @@ pe_status poly_eval_kernel_times(pe_poly *poly, double ms[3], uint64_t *runs);
 pe_status poly_eval_launches_per_run(pe_poly *poly, uint64_t T, uint32_t *launches);
 
 /*
+ * Sparse images (Algorithm 1 adds a coefficient c to b_t only when c != 0):
+ * turns dense T x G images (device, as written by poly_eval_run) into a CSR
+ * structure on the device.
+ *   row_ptr  : device, T+1 entries; image r's entries are [row_ptr[r], row_ptr[r+1]).
+ *   cols     : device, nonzero column indices (group g), ascending within a row.
+ *   vals     : device, the matching coefficients.
+ *   capacity : entries available in cols and vals.
+ *   nnz      : host; receives the number of nonzero coefficients.
+ * Synchronizes `stream` once (to learn nnz).  If nnz > capacity nothing is
+ * written to cols/vals and PE_ERR_ARG is returned with *nnz set, so the
+ * caller can retry with larger arrays.
+ */
+pe_status poly_eval_compact(const uint64_t *dense, uint64_t T, uint64_t G, uint64_t *row_ptr, uint32_t *cols,
+                            uint64_t *vals, uint64_t capacity, uint64_t *nnz, void *stream);
+
+/*
  * Step B for callers that cannot allocate device memory.  The paper has no
  * counterpart; it exists because some callers may not call cudaMalloc (code
  * inside another framework's memory pool, embedded runtimes without allocator

@@ -137,6 +137,7 @@ def lib():
             "poly_eval_modmul_peak": (st, [ctypes.c_int, _u64, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]),
             "poly_eval_int_pipe_rates": (st, [ctypes.POINTER(ctypes.c_double)]),
+            "poly_eval_compact": (st, [_vp, _u64, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -425,6 +426,22 @@ def modmul_peak(variant="barrett64", p: int = (1 << 61) - 1):
     tps, mhz = ctypes.c_double(), ctypes.c_double()
     _check(lib().poly_eval_modmul_peak(_variant(variant), int(p), ctypes.byref(tps), ctypes.byref(mhz)))
     return tps.value, mhz.value
+
+
+def compact(dense, stream=None):
+    """Sparse images from a dense (T, G) CUDA tensor: (row_ptr[T+1], cols, vals)
+    as CUDA tensors (int64, int32, int64 views of uint64 / uint32)."""
+    import torch
+    T, G = int(dense.shape[0]), int(dense.shape[1])
+    row_ptr = torch.empty(T + 1, dtype=torch.int64, device=dense.device)
+    cap = T * G
+    cols = torch.empty(max(cap, 1), dtype=torch.int32, device=dense.device)
+    vals = torch.empty(max(cap, 1), dtype=torch.int64, device=dense.device)
+    nnz = ctypes.c_uint64()
+    _check(lib().poly_eval_compact(dense.data_ptr(), T, G, row_ptr.data_ptr(), cols.data_ptr(), vals.data_ptr(),
+                                   cap, ctypes.byref(nnz), _stream_ptr(stream)))
+    n = int(nnz.value)
+    return row_ptr, cols[:n], vals[:n]
 
 
 def int_pipe_rates() -> dict:
