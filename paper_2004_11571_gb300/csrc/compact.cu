@@ -94,7 +94,7 @@ extern "C" pe_status poly_eval_compact(const uint64_t *dense, uint64_t T, uint64
                                        uint32_t *cols, uint64_t *vals, uint64_t capacity, uint64_t *nnz,
                                        void *stream)
 {
-    if (!nnz || (T && (!dense || !row_ptr)) || T > 0x7fffffffull || G > 0xffffffffull) {
+    if (!nnz || (T && !row_ptr) || (T && G && !dense) || T > 0x7fffffffull || G > 0xffffffffull) {
         set_error("bad arguments (device dense and row_ptr, host nnz; T < 2^31, G < 2^32)");
         return PE_ERR_ARG;
     }
