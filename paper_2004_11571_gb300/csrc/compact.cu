@@ -108,7 +108,7 @@ extern "C" pe_status poly_eval_compact(const uint64_t *dense, uint64_t T, uint64
             return cuda_fail(e, "compact");
         return PE_OK;
     }
-    // Row counts live in row_ptr[1..T] until the scan rewrites row_ptr in place.
+    // Row counts go to scratch; the scan writes row_ptr from them.
     DevBuf counts;
     if ((e = counts.ensure(T * 8, st)) != cudaSuccess) return cuda_fail(e, "compact scratch");
     k_count_rows<<<(unsigned)T, kCompactThreads, 0, st>>>(dense, G, counts.as<uint64_t>());
