@@ -247,3 +247,18 @@ def test_replanning_while_previous_run_is_in_flight():
         r, g = rnd.integers(0, T, 12), rnd.integers(0, cells.G, 12)
         assert np.array_equal(got[r, g], cells(r + t0, g))
     poly.close()
+
+
+def test_device_pointer_input_and_u32_exponents():
+    w = wl.make_zipf(n=6, s=12_000, p=P62, deg12=15, deg_rest=7, T=50, seed=27)
+    keys_ref, ref = oracle.eval_direct(w)
+    # terms already on the device (PE_FLAG_DEVICE_PTRS), 4-byte exponents
+    coeffs = torch.from_numpy(w.coeffs.view(np.int64).copy()).cuda()
+    exps = torch.from_numpy(w.exps.astype(np.int32)).cuda()
+    poly = pe.Poly(w.p, coeffs, exps)
+    assert np.array_equal(poly.groups(), keys_ref)
+    assert np.array_equal(pe.to_u64(poly.run(w.beta, w.T)), ref)
+    poly.close()
+    poly = pe.Poly(w.p, w.coeffs, w.exps.astype(np.uint32))          # host, 4-byte exponents
+    assert np.array_equal(pe.to_u64(poly.run(w.beta, w.T)), ref)
+    poly.close()
