@@ -70,6 +70,29 @@ __device__ __forceinline__ uint32_t barrett_mul32(uint32_t x, uint32_t w, uint32
     return x * w - __umulhi(x, wq) * p;
 }
 
+// The same value as barrett_mul_lazy4, with r = x*w + q*(2^64 - p) mod 2^64
+// accumulated by 32-bit multiply-adds (two wide, four low) instead of two
+// 64-bit products and a subtraction.  np = 2^64 - p.
+__device__ __forceinline__ uint64_t barrett_mul_lazy4_mad(uint64_t x, uint64_t w, uint64_t wq, uint64_t np)
+{
+    const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+    const uint32_t w0 = (uint32_t)w, w1 = (uint32_t)(w >> 32);
+    const uint32_t q0w = (uint32_t)wq, q1w = (uint32_t)(wq >> 32);
+    const uint64_t q = (uint64_t)x1 * q1w + __umulhi(x1, q0w) + __umulhi(x0, q1w);
+    const uint32_t q0 = (uint32_t)q, q1 = (uint32_t)(q >> 32);
+    const uint32_t n0 = (uint32_t)np, n1 = (uint32_t)(np >> 32);
+    uint64_t t;
+    uint32_t hi;
+    asm("mad.wide.u32 %0, %1, %2, 0;" : "=l"(t) : "r"(x0), "r"(w0));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(t) : "r"(q0), "r"(n0));
+    hi = (uint32_t)(t >> 32);
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(hi) : "r"(x0), "r"(w1));
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(hi) : "r"(x1), "r"(w0));
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(hi) : "r"(q0), "r"(n1));
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(hi) : "r"(q1), "r"(n0));
+    return ((uint64_t)hi << 32) | (uint32_t)t;
+}
+
 // Given mR = m * 2^64 mod p (canonical), the Barrett quotient of m is
 // (m*2^64 - mR) / p, an exact division, hence equal to -mR * p^-1 mod 2^64.
 __device__ __forceinline__ uint64_t barrett_quotient_from_mont(uint64_t mR, const ModCtx &mc)

@@ -119,11 +119,12 @@ __device__ __forceinline__ void lane_point(Lane<VAR> (&st)[K], const ModCtx &mc,
     } else {
         lo = 0;
         hi = 0;
+        const uint64_t np = 0ull - mc.p;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             add96(lo, hi, st[k].v);
             if constexpr (VAR == VAR_BARRETT)
-                st[k].v = barrett_mul_lazy4(st[k].v, st[k].w, st[k].wq, mc.p);
+                st[k].v = barrett_mul_lazy4_mad(st[k].v, st[k].w, st[k].wq, np);
             else
                 st[k].v = mont_mul(st[k].v, st[k].y, mc);
         }
