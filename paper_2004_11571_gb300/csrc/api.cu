@@ -243,6 +243,22 @@ Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
     t.kslabs = (uint32_t)k;
     t.Tc = (uint32_t)Tc;
     t.tailT = 0;
+    // Few items per warp: the run would end unevenly by a sizeable fraction.
+    // Reserve the last ~T/8 points for a band of one-slab, 64-point items that
+    // run after the others (their starting values are precomputed, so they are
+    // cheap), and make the other items twice as long.
+    const double items = (double)((slabs + k - 1) / k) * (double)((T + Tc - 1) / Tc);
+    if (!(f && (f->slabs || f->tchunk)) && T >= 512 && items / (double)R < 24.0) {
+        const uint64_t tail = std::min<uint64_t>(256, std::max<uint64_t>(64, (T / 8 + 32) / 64 * 64));
+        const uint64_t T0 = T - tail;
+        uint64_t q0 = (T0 + std::min<uint64_t>(512, 2 * Tc) - 1) / std::min<uint64_t>(512, 2 * Tc);
+        const uint64_t q1 = (tail + tail_tc(tail) - 1) / tail_tc(tail);
+        q0 = std::max<uint64_t>(1, std::min<uint64_t>(q0, lmax > q1 ? lmax - q1 : 1));
+        if (q0 + q1 <= lmax) {
+            t.Tc = (uint32_t)((T0 + q0 - 1) / q0);
+            t.tailT = (uint32_t)tail;
+        }
+    }
     return t;
 }
 
