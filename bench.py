@@ -46,7 +46,7 @@ OPS_PER_TP = {"barrett64": {"wide": 3, "hi": 2, "lo": 4}, "mont64": {"wide": 8, 
 NUM_SMS = 152
 # DRAM bytes (read + write) of one Step B launch on the large workload, from one
 # ncu capture of the current kernel; None for other workloads.
-STEPB_TRAFFIC_LARGE = 147_119_360
+STEPB_TRAFFIC_LARGE = None
 
 
 def parse():
