@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-burst", type=int, default=1500)
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
+    ap.add_argument("--no-tune", action="store_true", help="skip poly_eval_tune before timing")
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -237,6 +238,10 @@ def run_ours(args):
     t0, _ = sharding.weak_block(int(w.T), w.t0, rank)   # each rank: its own block of T points
     poly = pe.Poly.from_workload(w, variant=variant)
     G, T, s = poly.G, int(w.T), w.s
+    tuned = None
+    if not args.no_tune and variant in ("auto",):
+        tiles, tuned_ms = pe.tune(poly, T)          # measures tile shapes and products for this shape
+        tuned = {"tiles": tiles, "ms": tuned_ms}
     out = torch.empty((T, G), dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -320,7 +325,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": workload_config(w, args.config, variant, {"groups": G, "tiles": plan,
+            "config": workload_config(w, args.config, variant, {"groups": G, "tiles": plan, "tuned": tuned is not None,
                                                                "per_rank_points": f"t0 + rank*{T}"}),
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": "term-points/s", "h2d_bytes_per_step": int(h2d),

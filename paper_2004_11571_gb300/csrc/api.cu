@@ -223,6 +223,14 @@ Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
         t.Tc = (uint32_t)std::min<uint64_t>(f->tchunk, T - t.tailT);
         return t;
     }
+    if (te && te->kslabs && te->Tc && !(f && (f->slabs || f->tchunk || f->K))) {   // measured shape
+        t.kslabs = te->kslabs;
+        t.tailT = te->tail && te->tail + 32 <= T ? te->tail : 0;
+        t.Tc = (uint32_t)std::min<uint64_t>(te->Tc, T - t.tailT);
+        const uint64_t q0 = (T - t.tailT + t.Tc - 1) / t.Tc, q1 = t.tailT ? (t.tailT + 63) / 64 : 0;
+        if (q0 + q1 <= (uint64_t)kMaxStarts) return t;
+        t.tailT = 0;   // too many start rows for this T: fall through to the rule
+    }
     const uint64_t NC = count_chunks(P, t.K);
     int bps = 0;
     if (stepB_occupancy((int)t.K, P->variant, (int)t.wpb, &bps) != cudaSuccess || bps <= 0) bps = 1;

@@ -114,9 +114,49 @@ extern "C" pe_status poly_eval_tune(pe_poly *P, uint64_t T, pe_tiles *best, doub
         }
         if (result != PE_OK) break;
     }
+    // Item shape for the best product and chunk size: a few measured shapes
+    // around the rule's (slabs per item, points per item, tail band).
+    if (result == PE_OK) {
+        const uint32_t cand[][3] = {{1, 128, 0}, {2, 128, 0}, {1, 224, 128}, {2, 224, 128}, {1, 256, 0},
+                                    {2, 256, 0}, {1, 512, 0}, {2, 448, 128}};
+        for (const auto &c : cand) {
+            if (c[1] + c[2] > T) continue;
+            pe_tiles ft{};
+            ft.K = bestE.K;
+            ft.warps_per_block = bestE.wpb;
+            ft.slabs = c[0];
+            ft.tchunk = c[1];
+            ft.tail = c[2];
+            P->forced = ft;
+            P->requested_variant = bestE.variant;
+            P->plan.valid = false;
+            P->tail_plan.valid = false;
+            pe_status s = poly_eval_run(P, beta.data(), T, 1, out.as<uint64_t>(), st);
+            if (s != PE_OK) {
+                result = s;
+                break;
+            }
+            cudaEventRecord(a, st);
+            for (int r = 0; r < 3; ++r) poly_eval_run(P, beta.data(), T, 1, out.as<uint64_t>(), st);
+            cudaEventRecord(b, st);
+            if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
+                result = cuda_fail(e, "tune");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms / 3.0 < bestE.ms * 0.995) {
+                bestE.ms = ms / 3.0;
+                bestE.kslabs = c[0];
+                bestE.Tc = c[1];
+                bestE.tail = c[2];
+            }
+        }
+    }
     P->forced = saved_tiles;
     P->requested_variant = saved_req;
     P->plan.valid = false;
+    P->tail_plan.valid = false;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaStreamDestroy(st);
@@ -127,8 +167,6 @@ extern "C" pe_status poly_eval_tune(pe_poly *P, uint64_t T, pe_tiles *best, doub
     }
     if (best) {
         pe_tiles f{};
-        f.K = bestE.K;
-        f.warps_per_block = bestE.wpb;
         const Tiles t = choose_tiles(P, T, &f);
         best->K = t.K;
         best->slabs = t.kslabs;
@@ -153,7 +191,8 @@ extern "C" pe_status poly_eval_tune_save(const char *path)
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (const auto &kv : g_tune)
         f << "{\"key\": \"" << kv.first << "\", \"K\": " << kv.second.K << ", \"wpb\": " << kv.second.wpb
-          << ", \"variant\": " << kv.second.variant << ", \"ms\": " << kv.second.ms << "}\n";
+          << ", \"variant\": " << kv.second.variant << ", \"ms\": " << kv.second.ms << ", \"slabs\": "
+          << kv.second.kslabs << ", \"tchunk\": " << kv.second.Tc << ", \"tail\": " << kv.second.tail << "}\n";
     return PE_OK;
 }
 
@@ -187,6 +226,14 @@ extern "C" pe_status poly_eval_tune_load(const char *path)
         t.wpb = w;
         t.variant = v;
         t.ms = ms;
+        unsigned ks = 0, tc = 0, tl = 0;
+        const size_t sp = line.find("\"slabs\":");
+        if (sp != std::string::npos &&
+            sscanf(line.c_str() + sp, "\"slabs\": %u, \"tchunk\": %u, \"tail\": %u", &ks, &tc, &tl) == 3) {
+            t.kslabs = ks;
+            t.Tc = tc;
+            t.tail = tl;
+        }
         g_tune[line.substr(k0 + 8, k1 - k0 - 8)] = t;
     }
     return PE_OK;

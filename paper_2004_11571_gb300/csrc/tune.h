@@ -8,6 +8,7 @@ namespace pe {
 struct TuneEntry {
     uint32_t K = 0, wpb = 0;
     int variant = 0;
+    uint32_t kslabs = 0, Tc = 0, tail = 0;   // item shape (0: the library's rule)
     double ms = 0.0;
 };
 
