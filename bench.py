@@ -45,8 +45,18 @@ OPS_PER_TP = {"barrett64": {"wide": 3, "hi": 2, "lo": 4}, "mont64": {"wide": 8, 
               "barrett32": {"wide": 0, "hi": 1, "lo": 2}}
 NUM_SMS = 152
 # DRAM bytes (read + write) of one Step B launch on the large workload, from one
-# ncu capture of the current kernel; None for other workloads.
-STEPB_TRAFFIC_LARGE = None
+# ncu capture of the current kernel with the item shape it ran; reported only
+# when the timed plan has that same shape (None for other workloads).
+STEPB_TRAFFIC_LARGE = {"bytes": 61_555_200 + 71_791_872,
+                       "shape": {"K": 8, "slabs": 1, "tchunk": 224, "warps_per_block": 4, "tail_points": 128}}
+
+
+def stepb_traffic(config, vkey, plan):
+    """The captured DRAM bytes of Step B if the timed plan is the captured one."""
+    ref = STEPB_TRAFFIC_LARGE
+    if ref is None or config != "large" or vkey != "barrett64":
+        return None
+    return ref["bytes"] if all(plan.get(k) == v for k, v in ref["shape"].items()) else None
 
 
 def parse():
@@ -303,7 +313,7 @@ def run_ours(args):
         peak = NUM_SMS * rates["mad_lo"] * mhz * 1e6 / 1e9
         ach = tps_b * slots / 1e9
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gslot/s", "frac": ach / peak,
-                "traffic": STEPB_TRAFFIC_LARGE if args.config == "large" and vkey == "barrett64" else None,
+                "traffic": stepb_traffic(args.config, vkey, plan),
                 "kernel": "pe::k_stepB",
                 "peak_source": f"{NUM_SMS} SMs x {rates['mad_lo']:.1f} mad.lo.u32 per SM-clock (measured) x "
                                f"{mhz:.0f} MHz (median sampled SM clock)",
