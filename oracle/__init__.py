@@ -11,6 +11,9 @@ Functions (paper Sect. 2.3 definition of the bivariate images, Algorithm 1):
   eval_cells(w, t_abs, g)         -> values of chosen cells, O1 per cell
   eval_matrix(w)                  -> (keys, out[T,G])   O2, Algorithm 1 restated
   mulmod / addmod / powmod        -> the scalar F_p operations, for pins
+  power_sums(p, z, c, t0, K)      -> a_k = sum_i c_i z_i^(t0+k), k < K
+  tvandermonde_solve(p, z, a, t0) -> c with power_sums(p, z, c, t0, n) = a
+                                     (Gaussian elimination; Sect. 1 interpolation)
 """
 from __future__ import annotations
 
@@ -62,6 +65,12 @@ def _configure(lib):
     lib.oracle_eval_cells.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, _u64p,
                                       _u32p, _u64p, ctypes.c_uint64, _u64p, ctypes.c_uint64,
                                       _u64p, _u64p, _u64p]
+    lib.oracle_power_sums.restype = ctypes.c_int
+    lib.oracle_power_sums.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p, ctypes.c_uint64,
+                                      ctypes.c_uint64, _u64p]
+    lib.oracle_tvandermonde_solve.restype = ctypes.c_int
+    lib.oracle_tvandermonde_solve.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p,
+                                              ctypes.c_uint64, _u64p]
     return lib
 
 
@@ -177,3 +186,25 @@ class CellOracle:
 
 def eval_cells(w, t_abs, g):
     return CellOracle(w)(t_abs, g)
+
+
+def power_sums(p: int, z, c, t0: int, K: int) -> np.ndarray:
+    """a_k = sum_i c_i z_i^(t0+k) mod p for k = 0..K-1 (one coefficient's images)."""
+    z = np.ascontiguousarray(z, dtype=np.uint64)
+    c = np.ascontiguousarray(c, dtype=np.uint64)
+    a = np.zeros(max(K, 1), np.uint64)
+    if _load().oracle_power_sums(p, z.shape[0], _p(z, _u64p), _p(c, _u64p), t0, K, _p(a, _u64p)):
+        raise ValueError("oracle_power_sums: bad arguments")
+    return a[:K].copy()
+
+
+def tvandermonde_solve(p: int, z, a, t0: int):
+    """c solving sum_i c_i z_i^(t0+k) = a_k, k < n = len(z); None if singular."""
+    z = np.ascontiguousarray(z, dtype=np.uint64)
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    n = z.shape[0]
+    if a.shape[0] < n:
+        raise ValueError("need at least len(z) values")
+    c = np.zeros(max(n, 1), np.uint64)
+    rc = _load().oracle_tvandermonde_solve(p, n, _p(z, _u64p), _p(a, _u64p), t0, _p(c, _u64p))
+    return None if rc else c[:n].copy()

@@ -26,12 +26,23 @@
  *                        from power tables (Sect. 2.3), then T rounds of
  *                        a_i <- a_i * m_i followed by the coefficient
  *                        reduction over each group.  It is the CPU baseline.
+ *   oracle_power_sums  : the images of one (x1, x2) coefficient with known
+ *                        monomial values z_i: a_k = sum_i c_i z_i^(t0+k).
+ *   oracle_tvandermonde_solve : the inverse, interpolation from those images
+ *                        (Sect. 1: with points at successive powers of beta the
+ *                        linear systems of sparse interpolation are transposed
+ *                        Vandermonde systems).  The oracle is the definition:
+ *                        Gaussian elimination modulo p on the n x n system.
  *
  * Pins (tests under tests/): brute force with exact Python integers on tiny
  * inputs, Fermat's little theorem at Miller-Rabin-verified primes, the ring
  * homomorphisms eval(A+B) = eval(A)+eval(B) and eval(A*B) = eval(A)*eval(B),
  * the t0 = 0 and beta = 1 coefficient sums, the paper's gcd example
  * (Sect. 2.1) and small symmetric Toeplitz determinants (Sect. 2.2.1).
+ * The interpolation functions are pinned by closed forms for n = 1 and 2
+ * (Cramer's rule), exhaustive search over F_7^n, round trips through power
+ * sums computed with exact Python integers, and recovery of a polynomial's
+ * coefficients from images made by oracle_eval_direct.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -244,4 +255,70 @@ int oracle_eval_matrix(uint64_t p, uint32_t n, uint64_t s, const uint64_t *coeff
     }
     free(m); free(a); free(order); free(start); free(deg); free(tab); free(row);
     return 0;
+}
+
+/* ------------------------------------------ interpolation (Sect. 1) ---- */
+
+/*
+ * a_k = sum_{i<n} c_i * z_i^(t0+k) mod p for k = 0..K-1: the value at the
+ * point beta^(t0+k) of one (x1, x2) coefficient whose terms have monomial
+ * values z_i = M_i(beta) and coefficients c_i.
+ */
+int oracle_power_sums(uint64_t p, uint64_t n, const uint64_t *z, const uint64_t *c, uint64_t t0,
+                      uint64_t K, uint64_t *a)
+{
+    if (p < 2) return 1;
+    for (uint64_t k = 0; k < K; ++k) {
+        uint64_t acc = 0;
+        for (uint64_t i = 0; i < n; ++i)
+            acc = oracle_addmod(acc, oracle_mulmod(c[i] % p, oracle_powmod(z[i], t0 + k, p), p), p);
+        a[k] = acc;
+    }
+    return 0;
+}
+
+/*
+ * Solves sum_{i<n} c_i * z_i^(t0+k) = a_k (k = 0..n-1) for c by Gaussian
+ * elimination modulo the prime p: row k of the matrix holds z_i^(t0+k).  The
+ * pivot of each column is the first nonzero entry at or below the diagonal;
+ * inverses are a^(p-2) (Fermat).  Returns 0, or 1 if the matrix is singular
+ * (two equal z_i, or a zero z_i with t0 > 0).
+ */
+int oracle_tvandermonde_solve(uint64_t p, uint64_t n, const uint64_t *z, const uint64_t *a,
+                              uint64_t t0, uint64_t *c)
+{
+    if (p < 2) return 1;
+    if (n == 0) return 0;
+    uint64_t *A = (uint64_t *)malloc((size_t)n * (n + 1) * sizeof(uint64_t));  /* [A | a] */
+    for (uint64_t k = 0; k < n; ++k) {
+        for (uint64_t i = 0; i < n; ++i) A[k * (n + 1) + i] = oracle_powmod(z[i], t0 + k, p);
+        A[k * (n + 1) + n] = a[k] % p;
+    }
+    int singular = 0;
+    for (uint64_t col = 0; col < n && !singular; ++col) {
+        uint64_t piv = col;
+        while (piv < n && A[piv * (n + 1) + col] == 0) ++piv;
+        if (piv == n) { singular = 1; break; }
+        if (piv != col)
+            for (uint64_t j = 0; j <= n; ++j) {
+                uint64_t t = A[col * (n + 1) + j];
+                A[col * (n + 1) + j] = A[piv * (n + 1) + j];
+                A[piv * (n + 1) + j] = t;
+            }
+        uint64_t inv = oracle_powmod(A[col * (n + 1) + col], p - 2, p);
+        for (uint64_t j = col; j <= n; ++j) A[col * (n + 1) + j] = oracle_mulmod(A[col * (n + 1) + j], inv, p);
+        for (uint64_t r = 0; r < n; ++r) {                      /* eliminate the column elsewhere */
+            if (r == col) continue;
+            uint64_t f = A[r * (n + 1) + col];
+            if (f == 0) continue;
+            for (uint64_t j = col; j <= n; ++j) {
+                uint64_t sub = oracle_mulmod(f, A[col * (n + 1) + j], p);
+                A[r * (n + 1) + j] = oracle_addmod(A[r * (n + 1) + j], sub ? p - sub : 0, p);
+            }
+        }
+    }
+    if (!singular)
+        for (uint64_t i = 0; i < n; ++i) c[i] = A[i * (n + 1) + n];
+    free(A);
+    return singular;
 }

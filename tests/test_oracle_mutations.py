@@ -66,3 +66,52 @@ def test_pins_catch_mutant(name, tmp_path):
     assert src.count(old) >= 1, name
     lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "mut.so"))
     assert not _pins_hold(lib), f"pins accepted the planted mistake: {name}"
+
+
+# Mistakes planted in the interpolation functions (Sect. 1), caught by the
+# closed forms for one and two terms and round trips through power sums
+# computed with exact Python integers.
+INTERP_MUTANTS = {
+    "solver drops t0": ("A[k * (n + 1) + i] = oracle_powmod(z[i], t0 + k, p);",
+                        "A[k * (n + 1) + i] = oracle_powmod(z[i], k, p);"),
+    "power sums off by one": ("oracle_powmod(z[i], t0 + k, p), p), p);",
+                              "oracle_powmod(z[i], t0 + k + 1, p), p), p);"),
+    "elimination adds": ("sub ? p - sub : 0", "sub"),
+    "wrong inverse exponent": ("oracle_powmod(A[col * (n + 1) + col], p - 2, p)",
+                               "oracle_powmod(A[col * (n + 1) + col], p - 1, p)"),
+    "solution from the wrong column": ("c[i] = A[i * (n + 1) + n];", "c[i] = A[i * (n + 1) + n - 1];"),
+}
+
+
+def _interp_pins_hold(lib) -> bool:
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        for p in (101, 2**61 - 1):
+            rnd = random.Random(p)
+            for n in (1, 2, 5):
+                z = rnd.sample(range(1, min(p, 10**6)), n)
+                c = [rnd.randrange(p) for _ in range(n)]
+                for t0 in (0, 1, 3):
+                    exact = [sum(ci * pow(zi, t0 + k, p) for zi, ci in zip(z, c)) % p for k in range(n)]
+                    if oracle.power_sums(p, np.array(z, np.uint64), np.array(c, np.uint64), t0, n).tolist() != exact:
+                        return False
+                    got = oracle.tvandermonde_solve(p, np.array(z, np.uint64), np.array(exact, np.uint64), t0)
+                    if got is None or got.tolist() != c:
+                        return False
+        return True
+    finally:
+        oracle._lib = saved
+
+
+def test_unmutated_oracle_passes_interp_pins():
+    assert _interp_pins_hold(oracle._load())
+
+
+@pytest.mark.parametrize("name", sorted(INTERP_MUTANTS))
+def test_interp_pins_catch_mutant(name, tmp_path):
+    old, new = INTERP_MUTANTS[name]
+    src = oracle.source()
+    assert src.count(old) == 1, name
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "mut.so"))
+    assert not _interp_pins_hold(lib), f"pins accepted the planted mistake: {name}"

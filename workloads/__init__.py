@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "Workload", "is_prime", "random_prime", "make_uniform", "make_zipf",
     "config_tiny", "config_large", "config_width", "config_batched",
-    "served_requests", "sort_by_group", "shuffled",
+    "served_requests", "sort_by_group", "shuffled", "config_interp", "interp_group_sizes",
 ]
 
 MR_BASES = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
@@ -188,6 +188,7 @@ def make_zipf(*, n: int, s: int, p: int, deg12: int, deg_rest: int, T: int,
 # The five workload shapes (sizes as stated for the benchmark configurations).
 # ---------------------------------------------------------------------------
 SEED_TINY, SEED_LARGE, SEED_WIDTH, SEED_BATCH, SEED_SERVE = 1001, 2002, 3003, 4004, 5005
+SEED_INTERP = 6006
 
 
 def config_tiny(seed: int = SEED_TINY) -> Workload:
@@ -255,3 +256,65 @@ def served_requests(seed: int = SEED_SERVE, rate: float = 2000.0, duration: floa
             seen.append(k)
             reqs.append((t, k, None))
     return reqs
+
+
+def interp_group_sizes(s: int, u: int) -> np.ndarray:
+    """Sizes of the (x1, x2) coefficients of a polynomial to interpolate: s terms,
+    the largest coefficient exactly u terms, ceil(4s/u) coefficients whose sizes
+    follow rank^-a with a chosen by bisection as large as the cap u allows."""
+    if s <= u:
+        return np.array([s], np.int64)
+    G = -(-4 * s // u)
+    lo, hi = 0.0, 4.0
+    for _ in range(50):
+        a = 0.5 * (lo + hi)
+        if zipf_group_sizes(s, G, a)[0] > u:
+            hi = a
+        else:
+            lo = a
+    sizes = zipf_group_sizes(s, G, lo)
+    deficit = u - int(sizes[0])
+    sizes[0] = u
+    i = 1
+    while deficit > 0:                       # give the extra terms back, largest groups first
+        take = min(deficit, int(sizes[i]) - 1)
+        sizes[i] -= take
+        deficit -= take
+        i += 1
+    assert int(sizes.sum()) == s and int(sizes.max()) == u and sizes.min() >= 1
+    return sizes
+
+
+def config_interp(seed: int = SEED_INTERP, s: int = 34_937, u: int = 9_705, n: int = 14,
+                  bits: int = 62, deg_rest: int = 10) -> Workload:
+    """A polynomial to interpolate from its images (Sect. 1): s distinct terms,
+    (x1, x2) coefficients sized by interp_group_sizes (the largest u terms),
+    x3..xn exponents uniform in 0..deg_rest, distinct within each coefficient,
+    nonzero coefficients, T = u points from t0 = 1.  The defaults are the sizes
+    the paper gives for a factor of the m = 14 symmetric Toeplitz determinant
+    (34,937 terms, largest coefficient 9,705 terms)."""
+    if n < 3:
+        raise ValueError("n >= 3")
+    rng = _rng(seed)
+    p = random_prime(bits, seed + bits)
+    sizes = interp_group_sizes(s, u)
+    G = sizes.shape[0]
+    side = int(math.ceil(math.sqrt(G))) + 1
+    cells = rng.permutation(side * side)[:G]
+    dt = _exp_dtype(max(side, deg_rest))
+    exps = np.empty((s, n), dtype=dt)
+    at = 0
+    for g in range(G):
+        k = int(sizes[g])
+        rows: set = set()
+        while len(rows) < k:
+            for r in rng.integers(0, deg_rest + 1, size=(k - len(rows), n - 2)).tolist():
+                rows.add(tuple(r))
+        exps[at:at + k, 0] = cells[g] // side
+        exps[at:at + k, 1] = cells[g] % side
+        exps[at:at + k, 2:] = np.array(sorted(rows), dtype=dt)[rng.permutation(k)]
+        at += k
+    coeffs = _uniform_mod(rng, p, s, lo=1)
+    beta = _uniform_mod(rng, p, n - 2, lo=2)
+    return sort_by_group(Workload(p=p, n=n, coeffs=coeffs, exps=exps, beta=beta, T=u, t0=1,
+                                  name=f"interp n={n} s={s} G={G} u={u} p{bits}"))
