@@ -51,7 +51,8 @@ typedef enum {
     PE_ERR_CUDA = 7,          /* a CUDA runtime error (message in poly_eval_last_error) */
     PE_ERR_TIMEOUT = 8,       /* server poll: not finished within the timeout */
     PE_PENDING = 9,           /* server poll with zero timeout: still running */
-    PE_ERR_NOT_FOUND = 10     /* server: unknown ticket or resident polynomial */
+    PE_ERR_NOT_FOUND = 10,    /* server: unknown ticket or resident polynomial */
+    PE_ERR_SINGULAR = 11      /* interpolation: repeated monomial values, or a zero one with t0 > 0 */
 } pe_status;
 
 /*
@@ -214,6 +215,43 @@ pe_status poly_eval_launches_per_run(pe_poly *poly, uint64_t T, uint32_t *launch
  */
 pe_status poly_eval_compact(const uint64_t *dense, uint64_t T, uint64_t G, uint64_t *row_ptr, uint32_t *cols,
                             uint64_t *vals, uint64_t capacity, uint64_t *nnz, void *stream);
+
+/*
+ * Monomial values z_i = M_i(beta) (the m_i of Step A, Sect. 2.3), canonical
+ * in [0, p), in the library's term order: terms stably sorted by (d, e) in
+ * descending lexicographic order, so input that is already sorted keeps its
+ * order.  The terms of column g of the images are [off[g], off[g+1]).
+ *   beta : host, n-2 values in [1, p).
+ *   z    : device, s values (written on `stream`).
+ *   off  : host, G+1 values, or NULL.
+ * Errors: PE_ERR_ARG, PE_ERR_CUDA.
+ */
+pe_status poly_eval_monomials(pe_poly *poly, const uint64_t *beta, uint64_t *z, uint64_t *off, void *stream);
+
+/*
+ * Interpolation from images at successive powers (Sect. 1: with the points
+ * beta^t the linear systems of sparse interpolation are transposed
+ * Vandermonde systems).  For every column g with n_g = off[g+1] - off[g]
+ * terms, solves
+ *     sum_{i < n_g} c[off[g] + i] * z[off[g] + i]^(t0 + k) = images[k * lda + g],  k = 0..n_g-1,
+ * i.e. recovers the coefficients of one (x1, x2) coefficient of f from its
+ * first n_g images b_t0, b_t0+1, ... and its monomial values.  O(n_g^2)
+ * operations per column, all columns in parallel.
+ *   p      : odd prime, 3 <= p < 2^62.
+ *   off    : host, G+1 nondecreasing term offsets, off[0] = 0, off[G] < 2^32;
+ *            at most 2^24 terms per column.
+ *   z      : device, off[G] monomial values in [0, p), distinct within a column.
+ *   images : device, rows x lda uint64 (lda >= G), e.g. poly_eval_run's output
+ *            with lda = G; rows must be at least the largest n_g.
+ *   c      : device, off[G] outputs in [0, p).
+ * Synchronizes `stream` once (to read the status).  Errors: PE_ERR_PRIME,
+ * PE_ERR_ARG, PE_ERR_NOT_REDUCED (a node >= p), PE_ERR_SINGULAR (two equal
+ * nodes in a column, or a zero node with t0 > 0; the message names the
+ * column), PE_ERR_CUDA.
+ */
+pe_status poly_eval_vandermonde_solve(uint64_t p, uint64_t G, const uint64_t *off, const uint64_t *z,
+                                      const uint64_t *images, uint64_t rows, uint64_t lda, uint64_t t0,
+                                      uint64_t *c, void *stream);
 
 /*
  * Step B for callers that cannot allocate device memory.  The paper has no

@@ -32,8 +32,9 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "poly_eval.h")
 VARIANTS = {"auto": 0, "mont64": 1, "fp64": 2, "barrett64": 3, "barrett32": 4}
 STATUS = {0: "PE_OK", 1: "PE_ERR_ARG", 2: "PE_ERR_PRIME", 3: "PE_ERR_NOT_REDUCED", 4: "PE_ERR_EXP_RANGE",
           5: "PE_ERR_NOMEM", 6: "PE_ERR_ADMISSION", 7: "PE_ERR_CUDA", 8: "PE_ERR_TIMEOUT", 9: "PE_PENDING",
-          10: "PE_ERR_NOT_FOUND"}
+          10: "PE_ERR_NOT_FOUND", 11: "PE_ERR_SINGULAR"}
 PE_OK, PE_PENDING, PE_ERR_TIMEOUT, PE_ERR_ADMISSION = 0, 9, 8, 6
+PE_ERR_NOT_REDUCED, PE_ERR_SINGULAR = 3, 11
 FLAG_DEVICE_PTRS, FLAG_SORTED, FLAG_BORROW = 0x1, 0x2, 0x4
 
 
@@ -138,6 +139,8 @@ def lib():
                                            ctypes.POINTER(ctypes.c_double)]),
             "poly_eval_int_pipe_rates": (st, [ctypes.POINTER(ctypes.c_double)]),
             "poly_eval_compact": (st, [_vp, _u64, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
+            "poly_eval_monomials": (st, [_vp, _vp, _vp, _vp, _vp]),
+            "poly_eval_vandermonde_solve": (st, [_u64, _u64, _vp, _vp, _vp, _u64, _u64, _u64, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -240,6 +243,18 @@ class Poly:
         bptr = b.ctypes.data if b.size else None
         _check(lib().poly_eval_run(self._h, bptr, int(T), int(t0), ptr, _stream_ptr(stream)))
         return out
+
+    def monomials(self, beta: Sequence[int], stream=None):
+        """(z, off): the monomial values M_i(beta) as an int64 CUDA tensor of s
+        uint64 values in the library's term order (stable sort by (d, e)
+        descending), and the G+1 term offsets of the image columns (numpy)."""
+        import torch
+        b = np.ascontiguousarray(np.asarray(beta, dtype=np.uint64).reshape(-1))
+        z = torch.empty(max(self.s, 1), dtype=torch.int64, device="cuda")
+        off = np.zeros(self.G + 1, np.uint64)
+        _check(lib().poly_eval_monomials(self._h, b.ctypes.data if b.size else None, z.data_ptr(),
+                                         off.ctypes.data, _stream_ptr(stream)))
+        return z[: self.s], off
 
     def set_tiles(self, K=0, slabs=0, tchunk=0, warps_per_block=0, tail=0):
         t = _Tiles(K, slabs, tchunk, warps_per_block, tail)
@@ -442,6 +457,23 @@ def compact(dense, stream=None):
                                    cap, ctypes.byref(nnz), _stream_ptr(stream)))
     n = int(nnz.value)
     return row_ptr, cols[:n], vals[:n]
+
+
+def vandermonde_solve(p: int, off, z, images, t0: int = 1, out=None, stream=None):
+    """Coefficients c (int64 CUDA tensor of off[-1] uint64 values) with
+    sum_i c[off[g]+i] z[off[g]+i]^(t0+k) = images[k, g] for k < off[g+1]-off[g]:
+    interpolation of every image column from its monomial values (Sect. 1).
+    `z` and `images` are int64 CUDA tensors (uint64 values); `off` is host."""
+    import torch
+    off = np.ascontiguousarray(np.asarray(off, dtype=np.uint64).reshape(-1))
+    G = off.shape[0] - 1
+    s = int(off[-1]) if G >= 0 and off.size else 0
+    if out is None:
+        out = torch.empty(max(s, 1), dtype=torch.int64, device=z.device if _is_torch(z) else "cuda")
+    rows, lda = (int(images.shape[0]), int(images.stride(0))) if images.dim() == 2 else (0, G)
+    _check(lib().poly_eval_vandermonde_solve(int(p), G, off.ctypes.data, z.data_ptr(), images.data_ptr(), rows,
+                                             lda, int(t0), out.data_ptr(), _stream_ptr(stream)))
+    return out[:s]
 
 
 def int_pipe_rates() -> dict:

@@ -1,0 +1,353 @@
+// Interpolation from images at successive powers (Sect. 1).
+//
+// With evaluation points beta^t, t = t0, t0+1, ..., the images of one
+// (x1, x2) coefficient with n terms are a_k = sum_i c_i z_i^(t0+k), where
+// z_i = M_i(beta) is the value of the i-th monomial.  Recovering the c_i from
+// a_0..a_{n-1} is a transposed Vandermonde system (Zippel's observation,
+// Sect. 1), solved here in O(n^2) operations per coefficient:
+//
+//   P(z)  = prod_i (z - z_i) = sum_{j<=n} P_j z^j              (master polynomial)
+//   R_l   = sum_{k=0}^{n-1-l} a_k P_{k+1+l},   l = 0..n-1      (correlation of a and P)
+//   S_i   = R(z_i) = sum_l R_l z_i^l,   D_i = P'(z_i)
+//   c_i   = S_i / D_i * z_i^(-t0).
+//
+// Why: the quotient Q_i(z) = P(z) / (z - z_i) vanishes at every z_j, j != i,
+// and sum_k [z^k]Q_i * a_k = sum_j c_j z_j^t0 Q_i(z_j) = c_i z_i^t0 P'(z_i);
+// expanding [z^k]Q_i = sum_{j>k} P_j z_i^(j-1-k) gives S_i = R(z_i).
+//
+// Kernels (all coefficients of a call in each launch, flat tile lists built
+// on the host, 128 outputs per block):
+//   k_vdm_init   : leaves z - z_i of the product tree, images gathered per coefficient
+//   k_vdm_merge  : one level of the product tree: adjacent monic factors of
+//                  degree L multiplied pairwise (schoolbook, exact 128-bit
+//                  products summed in 192 bits, one reduction per output)
+//   k_vdm_corr   : R_l and P'_l
+//   k_vdm_solve  : S_i and D_i by Horner with the fixed multiplier z_i
+//                  (lazy Barrett product), then c_i
+// The work is integer multiplies: about n^2/2 exact products for the tree,
+// n^2/2 for the correlation and 2 n^2 fixed-multiplier products for Horner.
+#include <algorithm>
+#include <vector>
+#include "internal.h"
+#include "modarith.cuh"
+#include "kernels.h"
+
+namespace pe {
+
+constexpr int kVdmTile = 128;
+
+struct VdmTile {
+    uint32_t off;   // first term of the coefficient
+    uint32_t n;     // its number of terms
+    uint32_t j0;    // first output of the tile (index within the coefficient)
+    uint32_t g;     // coefficient (column of the images)
+};
+
+// (h, m, l) += a * b, exact (a, b < 2^64, h counts the carries out of 128 bits).
+__device__ __forceinline__ void mac192(uint64_t &l, uint64_t &m, uint32_t &h, uint64_t a, uint64_t b)
+{
+    asm("mad.lo.cc.u64 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u64 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+l"(l), "+l"(m), "+r"(h)
+        : "l"(a), "l"(b));
+}
+
+// (h*2^128 + m*2^64 + l) mod p, canonical, for h < p (the sums below stay far
+// under p * 2^128).  With R = 2^64: REDC(l) = l/R, REDC((h, m + l/R)) =
+// h + m/R + l/R^2 = x/R^2, and a Montgomery product by R^3 gives x.
+__device__ __forceinline__ uint64_t reduce192(uint64_t l, uint64_t m, uint32_t h, uint64_t r3, const ModCtx &mc)
+{
+    const uint64_t a = mont_redc(l, 0, mc);
+    uint64_t lo;
+    uint32_t hi = h;
+    asm("add.cc.u64 %0, %2, %3;\n\taddc.u32 %1, %1, 0;" : "=l"(lo), "+r"(hi) : "l"(m), "l"(a));
+    const uint64_t b = mont_redc(lo, hi, mc);
+    return canon(mont_mul(b, r3, mc), mc.p);
+}
+
+// Leaves: factor z - z_i stored as its constant coefficient p - z_i; images
+// of each coefficient gathered into consecutive words.  Flags nodes >= p.
+__global__ void k_vdm_init(const VdmTile *__restrict__ tiles, const uint64_t *__restrict__ z,
+                           const uint64_t *__restrict__ img, uint64_t lda, uint64_t p, uint64_t *__restrict__ leaf,
+                           uint64_t *__restrict__ ag, uint32_t *__restrict__ flags)
+{
+    const VdmTile t = tiles[blockIdx.x];
+    const uint32_t j = t.j0 + threadIdx.x;
+    if (j >= t.n) return;
+    const uint64_t zi = z[t.off + j];
+    if (zi >= p) atomicOr(flags, 1u);
+    leaf[t.off + j] = zi == 0 || zi >= p ? 0 : p - zi;
+    ag[t.off + j] = img[(uint64_t)j * lda + t.g];
+}
+
+// One level of the product tree: within a coefficient, the factors of terms
+// [2qL, 2qL+L) and [2qL+L, 2qL+2L) (monic, degrees la and lb, non-leading
+// coefficients stored in place of their terms) are multiplied; the product's
+// la+lb non-leading coefficients replace them.  A factor without a partner is
+// copied.
+__global__ void __launch_bounds__(kVdmTile) k_vdm_merge(const VdmTile *__restrict__ tiles, uint32_t L,
+                                                        const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
+                                                        uint64_t r3, ModCtx mc)
+{
+    const VdmTile t = tiles[blockIdx.x];
+    const uint32_t j = t.j0 + threadIdx.x;
+    if (j >= t.n) return;
+    const uint32_t base = j / (2 * L) * (2 * L);
+    const uint32_t la = min(L, t.n - base);
+    const uint32_t lb = min(L, t.n - base - la);
+    const uint32_t k = j - base;
+    const uint64_t *A = src + t.off + base;
+    const uint64_t *B = A + la;
+    if (lb == 0) {
+        dst[t.off + j] = A[k];
+        return;
+    }
+    uint64_t l = 0, m = 0;
+    uint32_t h = 0;
+    const uint32_t i_lo = k + 1 > lb ? k + 1 - lb : 0, i_hi = min(k, la - 1);
+    for (uint32_t i = i_lo; i <= i_hi; ++i) mac192(l, m, h, A[i], B[k - i]);
+    if (k >= la) mac192(l, m, h, 1, B[k - la]);   // A's leading 1
+    if (k >= lb) mac192(l, m, h, 1, A[k - lb]);   // B's leading 1
+    dst[t.off + j] = reduce192(l, m, h, r3, mc);
+}
+
+// R_l = sum_{k <= n-1-l} a_k P_{k+1+l} (P_n = 1) and P'_l = (l+1) P_{l+1}.
+// buf0/Rout0 and buf1/Rout1 are the same two buffers: each column reads its P
+// from one and writes its R to the other, so no element is both read and written.
+__global__ void __launch_bounds__(kVdmTile) k_vdm_corr(const VdmTile *__restrict__ tiles, const uint64_t *buf0,
+                                                       const uint64_t *buf1, const uint64_t *__restrict__ ag,
+                                                       uint64_t *Rout0, uint64_t *Rout1, uint64_t *__restrict__ Dout,
+                                                       uint64_t r3, ModCtx mc)
+{
+    const VdmTile t = tiles[blockIdx.x];
+    const uint32_t l = t.j0 + threadIdx.x;
+    if (l >= t.n) return;
+    // The tree leaves coefficient g's P in buffer (levels mod 2), levels = ceil(log2 n).
+    const uint32_t levels = t.n <= 1 ? 0 : 32 - __clz(t.n - 1);
+    const uint64_t *P = (levels & 1 ? buf1 : buf0) + t.off;
+    uint64_t *R = (levels & 1 ? Rout0 : Rout1) + t.off;   // the other buffer
+    const uint64_t *a = ag + t.off;
+    uint64_t lo = 0, mid = 0;
+    uint32_t h = 0;
+    const uint32_t kmax = t.n - 1 - l;                    // term k = kmax uses P_n = 1
+    for (uint32_t k = 0; k < kmax; ++k) mac192(lo, mid, h, a[k], P[k + 1 + l]);
+    mac192(lo, mid, h, 1, a[kmax]);
+    R[l] = reduce192(lo, mid, h, r3, mc);
+    uint64_t dl = 0, dm = 0;
+    uint32_t dh = 0;
+    mac192(dl, dm, dh, (uint64_t)l + 1, l + 1 < t.n ? P[l + 1] : 1);
+    Dout[t.off + l] = reduce192(dl, dm, dh, r3, mc);
+}
+
+// c_i = R(z_i) / P'(z_i) * z_i^(-t0).  Flags a zero P'(z_i) (repeated node)
+// or a zero node with t0 > 0 (bit 2) with the coefficient index.
+__global__ void __launch_bounds__(kVdmTile) k_vdm_solve(const VdmTile *__restrict__ tiles,
+                                                        const uint64_t *__restrict__ z,
+                                                        const uint64_t *__restrict__ Rb0,
+                                                        const uint64_t *__restrict__ Rb1,
+                                                        const uint64_t *__restrict__ D, uint64_t t0_exp, bool t0_pos,
+                                                        uint64_t *__restrict__ c, uint32_t *__restrict__ flags,
+                                                        ModCtx mc)
+{
+    const VdmTile t = tiles[blockIdx.x];
+    const uint32_t i = t.j0 + threadIdx.x;
+    if (i >= t.n) return;
+    const uint32_t levels = t.n <= 1 ? 0 : 32 - __clz(t.n - 1);
+    const uint64_t *R = (levels & 1 ? Rb0 : Rb1) + t.off;
+    const uint64_t *Dp = D + t.off;
+    const uint64_t zi = z[t.off + i];
+    const uint64_t p = mc.p, np = 0 - p;
+    const uint64_t zR = canon(mont_mul(zi, mc.r2, mc), p);
+    const uint64_t wq = barrett_quotient_from_mont(zR, mc);
+    uint64_t s = 0, d = 0;
+    for (uint32_t l = t.n; l-- > 0;) {
+        s = barrett_mul_lazy4_mad(s, zi, wq, np);     // [0, 4p)
+        d = barrett_mul_lazy4_mad(d, zi, wq, np);
+        s = (s >= mc.p2 ? s - mc.p2 : s) + R[l];      // [0, 3p)
+        d = (d >= mc.p2 ? d - mc.p2 : d) + Dp[l];
+    }
+    s = s >= mc.p2 ? s - mc.p2 : s;
+    s = canon(s, p);
+    d = d >= mc.p2 ? d - mc.p2 : d;
+    d = canon(d, p);
+    if (d == 0 || (zi == 0 && t0_pos)) {
+        atomicOr(flags, 2u);
+        atomicMin(flags + 1, t.g);
+        c[t.off + i] = 0;
+        return;
+    }
+    const uint64_t dinvR = mont_pow(canon(mont_mul(d, mc.r2, mc), p), p - 2, mc);   // d^-1 R (Fermat)
+    const uint64_t ztR = mont_pow(zR, t0_exp, mc);                                 // z^-t0 R
+    const uint64_t sR = canon(mont_mul(s, mc.r2, mc), p);
+    const uint64_t cR = mont_mul(mont_mul(sR, dinvR, mc), ztR, mc);
+    c[t.off + i] = canon(mont_redc(cR, 0, mc), p);
+}
+
+// Canonical values from Montgomery form.
+__global__ void k_from_mont(const uint64_t *__restrict__ xR, uint64_t s, ModCtx mc, uint64_t *__restrict__ x)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s; i += (uint64_t)gridDim.x * blockDim.x)
+        x[i] = canon(mont_redc(xR[i], 0, mc), mc.p);
+}
+
+static void add_tiles(std::vector<VdmTile> &v, uint32_t off, uint32_t n, uint32_t g)
+{
+    for (uint32_t j0 = 0; j0 < n; j0 += kVdmTile) v.push_back({off, n, j0, g});
+}
+
+}  // namespace pe
+
+using namespace pe;
+
+extern "C" pe_status poly_eval_vandermonde_solve(uint64_t p, uint64_t G, const uint64_t *off, const uint64_t *z,
+                                                 const uint64_t *images, uint64_t rows, uint64_t lda, uint64_t t0,
+                                                 uint64_t *c, void *stream)
+{
+    if (p < 3 || (p & 1) == 0 || p >= (1ull << 62)) {
+        set_error("p = %llu must be odd, at least 3 and below 2^62", (unsigned long long)p);
+        return PE_ERR_PRIME;
+    }
+    if (G && !off) {
+        set_error("off is NULL");
+        return PE_ERR_ARG;
+    }
+    if (G == 0) return PE_OK;
+    if (off[0] != 0 || off[G] > 0xffffffffull || G > 0xffffffffull) {
+        set_error("off[0] must be 0 and off[G] below 2^32");
+        return PE_ERR_ARG;
+    }
+    uint64_t nmax = 0;
+    for (uint64_t g = 0; g < G; ++g) {
+        if (off[g + 1] < off[g]) {
+            set_error("off must be nondecreasing (off[%llu] > off[%llu])", (unsigned long long)g,
+                      (unsigned long long)(g + 1));
+            return PE_ERR_ARG;
+        }
+        nmax = std::max(nmax, off[g + 1] - off[g]);
+    }
+    const uint64_t s = off[G];
+    if (s == 0) return PE_OK;
+    if (!z || !images || !c) {
+        set_error("z, images and c must be device pointers");
+        return PE_ERR_ARG;
+    }
+    if (nmax > (1ull << 24)) {
+        set_error("a coefficient has %llu terms; at most 2^24 are supported", (unsigned long long)nmax);
+        return PE_ERR_ARG;
+    }
+    if (nmax > rows || lda < G) {
+        set_error("a coefficient has %llu terms but the images have %llu rows (lda %llu, G %llu)",
+                  (unsigned long long)nmax, (unsigned long long)rows, (unsigned long long)lda,
+                  (unsigned long long)G);
+        return PE_ERR_ARG;
+    }
+    const ModCtx mc = make_modctx(p);
+    const uint64_t r3 = (uint64_t)(((unsigned __int128)mc.r2 * mc.r1) % p);
+    // Tile lists: level L of the tree covers coefficients with more than L
+    // terms; the other kernels cover all.  Larger coefficients first.
+    std::vector<uint64_t> order(G);
+    for (uint64_t g = 0; g < G; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint64_t a, uint64_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    std::vector<VdmTile> tiles;
+    std::vector<size_t> level_at;   // start of each tree level's tiles, then of the full list
+    for (uint64_t L = 1; L < nmax; L *= 2) {
+        level_at.push_back(tiles.size());
+        for (uint64_t g : order) {
+            const uint64_t n = off[g + 1] - off[g];
+            if (n > L) add_tiles(tiles, (uint32_t)off[g], (uint32_t)n, (uint32_t)g);
+        }
+    }
+    const size_t full_at = tiles.size();
+    for (uint64_t g : order) {
+        const uint64_t n = off[g + 1] - off[g];
+        if (n) add_tiles(tiles, (uint32_t)off[g], (uint32_t)n, (uint32_t)g);
+    }
+    level_at.push_back(full_at);
+    if (tiles.size() > 0x7fffffffull) {
+        set_error("too many columns");
+        return PE_ERR_ARG;
+    }
+    const uint32_t nfull = (uint32_t)(tiles.size() - full_at);
+
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    DevBuf dtiles, b0, b1, ag, dD, flags;
+    if ((e = dtiles.ensure(tiles.size() * sizeof(VdmTile))) != cudaSuccess ||
+        (e = b0.ensure(s * 8)) != cudaSuccess || (e = b1.ensure(s * 8)) != cudaSuccess ||
+        (e = ag.ensure(s * 8)) != cudaSuccess || (e = dD.ensure(s * 8)) != cudaSuccess ||
+        (e = flags.ensure(8)) != cudaSuccess)
+        return cuda_fail(e, "interpolation scratch");
+    const uint32_t fl_init[2] = {0, 0xffffffffu};
+    if ((e = cudaMemcpyAsync(dtiles.p, tiles.data(), tiles.size() * sizeof(VdmTile), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(flags.p, fl_init, 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "interpolation upload");
+    const VdmTile *T = dtiles.as<VdmTile>();
+    uint64_t *bufs[2] = {b0.as<uint64_t>(), b1.as<uint64_t>()};
+    k_vdm_init<<<nfull, kVdmTile, 0, st>>>(T + full_at, z, images, lda, p, bufs[0], ag.as<uint64_t>(),
+                                         flags.as<uint32_t>());
+    uint32_t L = 1;
+    for (size_t lv = 0; lv + 1 < level_at.size(); ++lv, L *= 2) {
+        const uint32_t nt = (uint32_t)(level_at[lv + 1] - level_at[lv]);
+        k_vdm_merge<<<nt, kVdmTile, 0, st>>>(T + level_at[lv], L, bufs[lv & 1], bufs[(lv + 1) & 1], r3, mc);
+    }
+    k_vdm_corr<<<nfull, kVdmTile, 0, st>>>(T + full_at, bufs[0], bufs[1], ag.as<uint64_t>(), bufs[0], bufs[1],
+                                         dD.as<uint64_t>(), r3, mc);
+    const uint64_t t0_exp = (p - 1 - t0 % (p - 1)) % (p - 1);
+    k_vdm_solve<<<nfull, kVdmTile, 0, st>>>(T + full_at, z, bufs[0], bufs[1], dD.as<uint64_t>(), t0_exp, t0 > 0, c,
+                                          flags.as<uint32_t>(), mc);
+    uint32_t fl[2] = {0, 0};
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(fl, flags.p, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "interpolation");
+    if (fl[0] & 1) {
+        set_error("a node z_i is not below p");
+        return PE_ERR_NOT_REDUCED;
+    }
+    if (fl[0] & 2) {
+        set_error("singular system in coefficient %u: repeated node, or a zero node with t0 > 0", fl[1]);
+        return PE_ERR_SINGULAR;
+    }
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_monomials(pe_poly *P, const uint64_t *beta, uint64_t *z, uint64_t *off, void *stream)
+{
+    if (!P) {
+        set_error("NULL poly");
+        return PE_ERR_ARG;
+    }
+    BetaArg barg;
+    pe_status st = check_beta(P, beta, &barg);
+    if (st != PE_OK) return st;
+    if (off) memcpy(off, P->group_off.data(), (P->G + 1) * sizeof(uint64_t));
+    if (P->s == 0) return PE_OK;
+    if (!z) {
+        set_error("z is NULL");
+        return PE_ERR_ARG;
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (P->last_use) {
+        cudaStreamWaitEvent(cs, P->last_use, 0);
+        cudaStreamWaitEvent(alloc_stream(), P->last_use, 0);
+    }
+    cudaError_t e;
+    const uint32_t dp1 = P->dmax + 1;
+    if ((e = P->ptab.ensure((size_t)std::max(1u, P->E * dp1) * 8)) != cudaSuccess ||
+        (e = P->mR.ensure(P->s * 8)) != cudaSuccess)
+        return cuda_fail(e, "monomial scratch");
+    if ((e = launch_powtab(barg, P->E, dp1, P->mc, P->ptab.as<uint64_t>(), cs)) != cudaSuccess ||
+        (e = launch_stepA(P->exps.p, P->exp_bytes, P->s, P->E, P->ptab.as<uint64_t>(), dp1, P->mc,
+                          P->mR.as<uint64_t>(), num_sms(), cs)) != cudaSuccess)
+        return cuda_fail(e, "Step A");
+    const unsigned grid = (unsigned)std::min<uint64_t>((P->s + 255) / 256, (uint64_t)num_sms() * 8);
+    k_from_mont<<<grid, 256, 0, cs>>>(P->mR.as<uint64_t>(), P->s, P->mc, z);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "monomials");
+    if (!P->last_use && (e = cudaEventCreateWithFlags(&P->last_use, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "event");
+    if ((e = cudaEventRecord(P->last_use, cs)) != cudaSuccess) return cuda_fail(e, "event");
+    return PE_OK;
+}
