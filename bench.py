@@ -198,6 +198,77 @@ def bench_compact(pe, dense, torch, reps=20):
             "note": "host-timed, includes one stream synchronization per call"}
 
 
+def _vdm_counts(off):
+    """Algorithmic multiplies of the solver: exact 64x64-bit products of the
+    product tree and of the correlation, fixed-multiplier products of Horner."""
+    tree = corr = horner = n2 = 0
+    for g in range(len(off) - 1):
+        n = int(off[g + 1] - off[g])
+        L = 1
+        while L < n:
+            for base in range(0, n, 2 * L):
+                la = min(L, n - base)
+                tree += la * min(L, n - base - la)
+            L *= 2
+        corr += n * (n - 1) // 2
+        horner += 2 * n * n
+        n2 += n * n
+    return tree, corr, horner, n2
+
+
+def bench_interp(pe, torch, mhz, reps=10):
+    """Interpolation from images (Sect. 1) after an evaluation at T = u points:
+    a factor of the m = 14 symmetric Toeplitz determinant by size (34,937
+    terms, largest coefficient 9,705 terms) and the gcd benchmark's g by size
+    (10^4 terms, largest coefficient 122 terms)."""
+    rates = pe.int_pipe_rates()
+    wide = rates["mad_lo"] / rates["mad_wide"]
+    slots_exact = 4 * wide
+    slots_b = sum(n * c for n, c in zip(OPS_PER_TP["barrett64"].values(),
+                                        (wide, rates["mad_lo"] / rates["mad_hi"], 1.0)))
+    peak = NUM_SMS * rates["mad_lo"] * mhz * 1e6 / 1e9
+    res = []
+    for w in (wl.config_interp(), wl.config_interp(seed=wl.SEED_INTERP + 1, s=10_000, u=122, n=9)):
+        poly = pe.Poly.from_workload(w)
+        images = poly.run(w.beta, w.T, t0=1)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        images = poly.run(w.beta, w.T, t0=1)
+        torch.cuda.synchronize()
+        eval_ms = (time.perf_counter() - t) * 1e3
+        z, off = poly.monomials(w.beta)
+        for _ in range(3):
+            c = pe.vandermonde_solve(w.p, off, z, images, t0=1)
+        pe.vandermonde_timing(True)
+        kms = {"leaves": 0.0, "tree": 0.0, "correlation": 0.0, "horner": 0.0}
+        t = time.perf_counter()
+        for _ in range(reps):
+            c = pe.vandermonde_solve(w.p, off, z, images, t0=1)
+            for k, v in pe.vandermonde_timing().items():
+                kms[k] += v / reps
+        dt = (time.perf_counter() - t) / reps
+        pe.vandermonde_timing(False)
+        exact = pe.to_u64(c).tolist() == w.coeffs.tolist()
+        tree, corr, horner, n2 = _vdm_counts(off)
+        ach = horner * slots_b / (kms["horner"] * 1e-3) / 1e9 if kms["horner"] > 0 else None
+        res.append({"workload": w.name, "terms": w.s, "columns": int(poly.G), "max_terms": int(w.T),
+                    "sum_n2": n2, "exact": exact, "ms": dt * 1e3, "terms_per_s": w.s / dt, "n2_per_s": n2 / dt,
+                    "kernel_ms": kms, "eval_images_ms": eval_ms,
+                    "multiplies": {"tree_exact": tree, "correlation_exact": corr, "horner_fixed": horner},
+                    "roofline": {"kernel": "pe::k_vdm_solve", "bound": "alu", "unit": "Gslot/s",
+                                 "achieved": ach, "peak": peak, "frac": ach / peak if ach else None,
+                                 "algorithmic": f"2 n^2 lazy Barrett products per column ({slots_b:.2f} mad.lo "
+                                                f"slots each) = {horner} products",
+                                 "tree_frac": (tree * slots_exact / (kms["tree"] * 1e-3) / 1e9 / peak
+                                               if kms["tree"] > 0 else None),
+                                 "correlation_frac": (corr * slots_exact / (kms["correlation"] * 1e-3) / 1e9 / peak
+                                                      if kms["correlation"] > 0 else None)},
+                    "note": "ms is host-timed per call (tile upload, five or more launches, one synchronization)"})
+        poly.close()
+        del images, z, c
+    return res
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -348,6 +419,7 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_stride)
     if world == 1 and not args.no_extras:
         line["sparse_images"] = bench_compact(pe, out, torch)
+        line["interpolation"] = bench_interp(pe, torch, mhz)
     poly.close()
     if world == 1 and not args.no_extras:
         del out, flush

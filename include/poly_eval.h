@@ -254,6 +254,15 @@ pe_status poly_eval_vandermonde_solve(uint64_t p, uint64_t G, const uint64_t *of
                                       uint64_t *c, void *stream);
 
 /*
+ * Kernel timing of poly_eval_vandermonde_solve on the calling host thread.
+ * enable > 0 turns event timing on for later calls, 0 turns it off, < 0
+ * leaves it unchanged.  If ms != NULL it receives the kernel times in
+ * milliseconds of the latest timed call: ms[0] leaves and image gather,
+ * ms[1] product tree (all levels), ms[2] correlation, ms[3] Horner and solve.
+ */
+pe_status poly_eval_vandermonde_timing(int enable, double ms[4]);
+
+/*
  * Step B for callers that cannot allocate device memory.  The paper has no
  * counterpart; it exists because some callers may not call cudaMalloc (code
  * inside another framework's memory pool, embedded runtimes without allocator

@@ -141,6 +141,7 @@ def lib():
             "poly_eval_compact": (st, [_vp, _u64, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
             "poly_eval_monomials": (st, [_vp, _vp, _vp, _vp, _vp]),
             "poly_eval_vandermonde_solve": (st, [_u64, _u64, _vp, _vp, _vp, _u64, _u64, _u64, _vp, _vp]),
+            "poly_eval_vandermonde_timing": (st, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -474,6 +475,14 @@ def vandermonde_solve(p: int, off, z, images, t0: int = 1, out=None, stream=None
     _check(lib().poly_eval_vandermonde_solve(int(p), G, off.ctypes.data, z.data_ptr(), images.data_ptr(), rows,
                                              lda, int(t0), out.data_ptr(), _stream_ptr(stream)))
     return out[:s]
+
+
+def vandermonde_timing(enable=None) -> dict:
+    """Kernel milliseconds of the latest timed vandermonde_solve on this thread;
+    enable=True/False switches timing for later calls."""
+    ms = (ctypes.c_double * 4)()
+    _check(lib().poly_eval_vandermonde_timing(-1 if enable is None else int(bool(enable)), ms))
+    return {"leaves": ms[0], "tree": ms[1], "correlation": ms[2], "horner": ms[3]}
 
 
 def int_pipe_rates() -> dict:
