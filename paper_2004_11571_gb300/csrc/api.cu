@@ -450,6 +450,134 @@ static pe_status check_prime(uint64_t p, int variant)
     return PE_OK;
 }
 
+// Terms already in group order are checked, grouped and packed on the device
+// (create.cu): the host only copies the raw arrays into page-locked staging
+// (several threads) and reads back the flags and the group table.  Sets
+// *fallback, and does nothing else, when the terms are not in group order or
+// staging memory is unavailable; the host path then handles them.
+static constexpr uint64_t kDeviceCreateMin = 1u << 14;
+
+static pe_status create_poly_device(const pe_poly_desc *d, int variant, pe_poly **out, bool host_threads,
+                                    bool *fallback)
+{
+    *fallback = false;
+    const uint64_t s = d->s;
+    const uint32_t n = d->n, w = d->exp_bytes, E = n - 2;
+    const size_t cbytes = s * 8, ebytes = (size_t)s * n * w;
+    const bool dev_in = (d->flags & PE_FLAG_DEVICE_PTRS) != 0;
+    const uint64_t nb = (s + 1023) / 1024;
+    std::unique_ptr<pe_poly> P(new pe_poly());
+    DevBuf raw, keys, counts, base, goff, gkeys, info;
+    Staging stg{};
+    cudaStream_t us = upload_stream_acquire();
+    auto finish = [&]() {   // waits for queued work before the scratch is freed
+        cudaStreamSynchronize(us);
+        upload_stream_release(us);
+        stage_release(stg);
+    };
+    cudaError_t e;
+    if ((e = P->coeffs.ensure(cbytes, us)) != cudaSuccess || (!dev_in && (e = raw.ensure(ebytes, us)) != cudaSuccess) ||
+        (e = keys.ensure(s * 8, us)) != cudaSuccess || (e = counts.ensure(nb * 8, us)) != cudaSuccess ||
+        (e = base.ensure((nb + 1) * 8, us)) != cudaSuccess || (e = goff.ensure(s * 8, us)) != cudaSuccess ||
+        (e = gkeys.ensure(s * 8, us)) != cudaSuccess || (e = info.ensure(sizeof(CreateInfo), us)) != cudaSuccess ||
+        (e = P->mR.ensure(s * 8, us)) != cudaSuccess) {
+        finish();
+        return cuda_fail(e, "device allocation");
+    }
+    const void *dexps = d->exps;
+    if (!dev_in) {
+        stg = stage_acquire(cbytes + ebytes);
+        if (!stg.p) {
+            finish();
+            *fallback = true;
+            return PE_OK;
+        }
+        unsigned char *dst = (unsigned char *)stg.p;
+        const unsigned nth = host_threads ? std::max(1u, std::min(16u, std::thread::hardware_concurrency())) : 1u;
+        auto copy = [&](unsigned t) {
+            const size_t c0 = cbytes * t / nth, c1 = cbytes * (t + 1) / nth;
+            const size_t e0 = ebytes * t / nth, e1 = ebytes * (t + 1) / nth;
+            memcpy(dst + c0, (const unsigned char *)d->coeffs + c0, c1 - c0);
+            memcpy(dst + cbytes + e0, (const unsigned char *)d->exps + e0, e1 - e0);
+        };
+        if (nth == 1) {
+            copy(0);
+        } else {
+            std::vector<std::thread> th;
+            for (unsigned t = 0; t < nth; ++t) th.emplace_back(copy, t);
+            for (std::thread &x : th) x.join();
+        }
+        if ((e = cudaMemcpyAsync(P->coeffs.p, dst, cbytes, cudaMemcpyHostToDevice, us)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(raw.p, dst + cbytes, ebytes, cudaMemcpyHostToDevice, us)) != cudaSuccess) {
+            finish();
+            return cuda_fail(e, "uploading terms");
+        }
+        dexps = raw.p;
+    } else if ((e = cudaMemcpyAsync(P->coeffs.p, d->coeffs, cbytes, cudaMemcpyDeviceToDevice, us)) != cudaSuccess) {
+        finish();
+        return cuda_fail(e, "copying terms");
+    }
+    CreateInfo ci{};
+    uint64_t G = 0;
+    if ((e = cudaMemsetAsync(info.p, 0, sizeof(CreateInfo), us)) != cudaSuccess ||
+        (e = cudaMemsetAsync(info.p, 0xff, sizeof(unsigned long long), us)) != cudaSuccess ||
+        (e = launch_term_scan(P->coeffs.as<uint64_t>(), dexps, w, s, n, d->p, keys.as<uint64_t>(),
+                              info.as<CreateInfo>(), counts.as<uint64_t>(), base.as<uint64_t>(), goff.as<uint64_t>(),
+                              gkeys.as<uint32_t>(), us)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&ci, info.p, sizeof ci, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&G, base.as<uint64_t>() + nb, 8, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(us)) != cudaSuccess) {
+        finish();
+        return cuda_fail(e, "scanning terms");
+    }
+    if (ci.bad != ~0ull) {
+        uint64_t v = 0;
+        if (dev_in)
+            cudaMemcpy(&v, d->coeffs + ci.bad, 8, cudaMemcpyDeviceToHost);
+        else
+            v = d->coeffs[ci.bad];
+        finish();
+        set_error("coefficient %llu of term %llu is not reduced mod p", (unsigned long long)v, ci.bad);
+        return PE_ERR_NOT_REDUCED;
+    }
+    if (ci.unsorted) {
+        finish();
+        *fallback = true;
+        return PE_OK;
+    }
+    if (ci.dmax > 0xffff) {
+        finish();
+        set_error("exponent %u above 65535", ci.dmax);
+        return PE_ERR_EXP_RANGE;
+    }
+    P->p = d->p;
+    P->n = n;
+    P->E = E;
+    P->s = s;
+    P->requested_variant = variant;
+    P->variant = variant == PE_MODMUL_AUTO ? default_variant(d->p) : variant;
+    P->mc = make_modctx(d->p);
+    P->dmax = ci.dmax;
+    P->exp_bytes = ci.dmax <= 0xff ? 1 : 2;
+    P->G = G;
+    P->group_off.resize(G + 1);
+    P->keys.resize(2 * G);
+    const size_t dp1 = ci.dmax + 1;
+    if ((e = P->exps.ensure((size_t)E * s * P->exp_bytes, us)) != cudaSuccess ||
+        (e = P->ptab.ensure((size_t)E * dp1 * 8, us)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P->group_off.data(), goff.p, G * 8, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P->keys.data(), gkeys.p, 2 * G * 4, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
+        (e = launch_pack_exps(dexps, w, s, n, P->exp_bytes, P->exps.p, us)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(us)) != cudaSuccess) {
+        finish();
+        return cuda_fail(e, "packing terms");
+    }
+    P->group_off[G] = s;
+    finish();
+    *out = P.release();
+    return PE_OK;
+}
+
 }  // namespace pe
 
 using namespace pe;
@@ -493,6 +621,11 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
     }
     pe_status st = check_prime(d->p, variant);
     if (st != PE_OK) return st;
+    if (d->s >= kDeviceCreateMin) {
+        bool fallback = false;
+        st = create_poly_device(d, variant, out, host_threads, &fallback);
+        if (!fallback) return st;
+    }
 
     const uint64_t s = d->s;
     const uint32_t n = d->n, E = n - 2, w = d->exp_bytes;

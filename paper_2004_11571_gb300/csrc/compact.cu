@@ -8,6 +8,7 @@
 // column order using a block-wide prefix of per-warp ballots.  The work is a
 // streaming read of the dense images: HBM-bound.
 #include "internal.h"
+#include "kernels.h"
 
 namespace pe {
 
@@ -84,6 +85,12 @@ __global__ void __launch_bounds__(kCompactThreads) k_write_rows(const uint64_t *
         base += total;
         __syncthreads();
     }
+}
+
+cudaError_t launch_scan_counts(const uint64_t *counts, uint64_t n, uint64_t *out, cudaStream_t st)
+{
+    k_scan_rows<<<1, 1024, 0, st>>>(counts, n, out);
+    return cudaGetLastError();
 }
 
 }  // namespace pe

@@ -18,4 +18,19 @@ cudaError_t launch_stepB(int K, int var, const StepBJob &J0, uint32_t n0, const 
                          cudaStream_t st);
 cudaError_t stepB_occupancy(int K, int var, int wpb, int *blocks_per_sm);
 
+// Exclusive scan of n counts into out[0..n] (out[n] = total), one block.
+cudaError_t launch_scan_counts(const uint64_t *counts, uint64_t n, uint64_t *out, cudaStream_t st);
+
+// Device side of poly_eval_create (create.cu).
+struct CreateInfo {
+    unsigned long long bad;   // lowest index of a coefficient >= p, or ~0
+    uint32_t dmax;            // largest exponent of x3..xn
+    uint32_t unsorted;        // nonzero if some (d, e) key exceeds the previous one
+};
+cudaError_t launch_term_scan(const uint64_t *coeffs, const void *exps, uint32_t width, uint64_t s, uint32_t n,
+                             uint64_t p, uint64_t *keys, CreateInfo *info, uint64_t *counts, uint64_t *base,
+                             uint64_t *goff, uint32_t *gkeys, cudaStream_t st);
+cudaError_t launch_pack_exps(const void *exps, uint32_t width, uint64_t s, uint32_t n, uint32_t out_bytes,
+                             void *out, cudaStream_t st);
+
 }  // namespace pe
