@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <atomic>
+#include <condition_variable>
 #include <mutex>
 #include <numeric>
 #include <memory>
@@ -146,6 +148,92 @@ void stage_release(Staging s)
 }
 }  // namespace
 
+// ----------------------------------------------------------- host pool
+namespace {
+struct HostPool {
+    // A job is published with a new generation; workers that pick it up are
+    // counted in `active`, and run() returns only when every index is done and
+    // no worker is still inside the job, so no worker ever holds a finished job.
+    std::mutex run_mu;                 // one parallel call at a time
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::vector<std::thread> threads;
+    const std::function<void(unsigned)> *job = nullptr;
+    unsigned n = 0, finished = 0, active = 0;
+    std::atomic<unsigned> next{0};
+    uint64_t gen = 0;
+    bool stop = false;
+    HostPool()
+    {
+        const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        for (unsigned t = 1; t < hw; ++t) threads.emplace_back([this] { work(); });
+    }
+    void drain(const std::function<void(unsigned)> &fn, unsigned count)
+    {
+        unsigned done = 0;
+        for (unsigned i; (i = next.fetch_add(1)) < count;) {
+            fn(i);
+            ++done;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        finished += done;
+    }
+    void work()
+    {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv.wait(lk, [&] { return stop || gen != seen; });
+            if (stop) return;
+            seen = gen;
+            if (!job) continue;
+            const std::function<void(unsigned)> *f = job;
+            const unsigned count = n;
+            ++active;
+            lk.unlock();
+            drain(*f, count);
+            lk.lock();
+            --active;
+            done_cv.notify_all();
+        }
+    }
+    void run(unsigned count, const std::function<void(unsigned)> &fn)
+    {
+        std::lock_guard<std::mutex> rl(run_mu);
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            done_cv.wait(lk, [&] { return active == 0; });
+            job = &fn;
+            n = count;
+            finished = 0;
+            next.store(0);
+            ++gen;
+        }
+        cv.notify_all();
+        drain(fn, count);
+        std::unique_lock<std::mutex> lk(mu);
+        done_cv.wait(lk, [&] { return finished == count && active == 0; });
+        job = nullptr;
+    }
+};
+HostPool &host_pool()
+{
+    static HostPool *pool = new HostPool();   // never destroyed: workers may outlive static destructors
+    return *pool;
+}
+}  // namespace
+
+void host_parallel(unsigned n, const std::function<void(unsigned)> &fn)
+{
+    if (n <= 1) {
+        if (n) fn(0);
+        return;
+    }
+    host_pool().run(n, fn);
+}
+
+unsigned host_pool_size() { return (unsigned)host_pool().threads.size() + 1; }
+
 int num_sms()
 {
     static int n = 0;
@@ -275,18 +363,24 @@ void build_chunks(pe_poly *P, uint32_t K)
     HostChunks &h = P->chunks;
     if (h.K == K && !h.cs.empty()) return;
     h.K = K;
-    h.cs.clear();
-    h.cg.clear();
-    h.gfirst.assign(P->G + 1, 0);
+    h.gfirst.resize(P->G + 1);
+    uint64_t nc = 0;
     for (uint64_t g = 0; g < P->G; ++g) {
-        h.gfirst[g] = (uint32_t)h.cg.size();
-        for (uint64_t st = P->group_off[g]; st < P->group_off[g + 1]; st += K) {
-            h.cs.push_back((uint32_t)st);
-            h.cg.push_back((uint32_t)g);
+        h.gfirst[g] = (uint32_t)nc;
+        nc += (P->group_off[g + 1] - P->group_off[g] + K - 1) / K;
+    }
+    h.gfirst[P->G] = (uint32_t)nc;
+    h.cs.resize(nc + 1);
+    h.cg.resize(nc);
+    uint32_t *cs = h.cs.data(), *cg = h.cg.data();
+    for (uint64_t g = 0; g < P->G; ++g) {
+        uint64_t c = h.gfirst[g];
+        for (uint64_t st = P->group_off[g]; st < P->group_off[g + 1]; st += K, ++c) {
+            cs[c] = (uint32_t)st;
+            cg[c] = (uint32_t)g;
         }
     }
-    h.gfirst[P->G] = (uint32_t)h.cg.size();
-    h.cs.push_back((uint32_t)P->s);
+    cs[nc] = (uint32_t)P->s;
 }
 
 void build_plan_host(pe_poly *P, const Tiles &t, uint64_t T, PlanHost &ph)
@@ -374,7 +468,7 @@ void fill_job(StepBJob &J, pe_poly *P, const PlanHost &ph, const uint32_t *cs, c
     J.mc = P->mc;
 }
 
-pe_status ensure_plan(pe_poly *P, Plan &pl, const Tiles &t, uint64_t T)
+pe_status ensure_plan(pe_poly *P, Plan &pl, const Tiles &t, uint64_t T, cudaStream_t st, bool queued)
 {
     if (pl.valid && pl.K == t.K && pl.kslabs == t.kslabs && pl.Tc == t.Tc && pl.T == T && pl.wpb == t.wpb)
         return PE_OK;
@@ -383,19 +477,31 @@ pe_status ensure_plan(pe_poly *P, Plan &pl, const Tiles &t, uint64_t T)
     build_plan_host(P, t, T, ph);
     const HostChunks &h = P->chunks;
     cudaError_t e;
-    if ((e = pl.cs.ensure(h.cs.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
-    if ((e = pl.cg.ensure(std::max<size_t>(h.cg.size(), 1) * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
-    if ((e = pl.unit.ensure(ph.unit.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
-    if ((e = pl.span.ensure(ph.span.size() * 4)) != cudaSuccess) return cuda_fail(e, "plan alloc");
-    if ((e = pl.counters.ensure(ph.counter_bytes())) != cudaSuccess) return cuda_fail(e, "plan alloc");
-    if ((e = pl.carry.ensure(ph.carry_bytes())) != cudaSuccess) return cuda_fail(e, "carry alloc");
-    if ((e = pl.chain.ensure(ph.chain_bytes())) != cudaSuccess) return cuda_fail(e, "chain alloc");
-    if ((e = cudaMemcpy(pl.cs.p, h.cs.data(), h.cs.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (ph.NC && (e = cudaMemcpy(pl.cg.p, h.cg.data(), h.cg.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) ||
-        (e = cudaMemcpy(pl.unit.p, ph.unit.data(), ph.unit.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(pl.span.p, ph.span.data(), ph.span.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(pl.counters.p, 0, pl.counters.bytes)) != cudaSuccess)
+    auto alloc = [&](DevBuf &b, size_t n) { return queued ? b.ensure_async(n, st) : b.ensure(n); };
+    if ((e = alloc(pl.cs, h.cs.size() * 4)) != cudaSuccess || (e = alloc(pl.cg, std::max<size_t>(h.cg.size(), 1) * 4)) != cudaSuccess ||
+        (e = alloc(pl.unit, ph.unit.size() * 4)) != cudaSuccess || (e = alloc(pl.span, ph.span.size() * 4)) != cudaSuccess ||
+        (e = alloc(pl.counters, ph.counter_bytes())) != cudaSuccess)
+        return cuda_fail(e, "plan alloc");
+    if ((e = alloc(pl.carry, ph.carry_bytes())) != cudaSuccess) return cuda_fail(e, "carry alloc");
+    if ((e = alloc(pl.chain, ph.chain_bytes())) != cudaSuccess) return cuda_fail(e, "chain alloc");
+    if (queued) {
+        // Pageable sources are staged by the driver before these calls return.
+        if ((e = cudaMemcpyAsync(pl.cs.p, h.cs.data(), h.cs.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (ph.NC && (e = cudaMemcpyAsync(pl.cg.p, h.cg.data(), h.cg.size() * 4, cudaMemcpyHostToDevice, st)) !=
+                          cudaSuccess) ||
+            (e = cudaMemcpyAsync(pl.unit.p, ph.unit.data(), ph.unit.size() * 4, cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(pl.span.p, ph.span.data(), ph.span.size() * 4, cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess ||
+            (e = cudaMemsetAsync(pl.counters.p, 0, pl.counters.bytes, st)) != cudaSuccess)
+            return cuda_fail(e, "plan upload");
+    } else if ((e = cudaMemcpy(pl.cs.p, h.cs.data(), h.cs.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+               (ph.NC && (e = cudaMemcpy(pl.cg.p, h.cg.data(), h.cg.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+               (e = cudaMemcpy(pl.unit.p, ph.unit.data(), ph.unit.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+               (e = cudaMemcpy(pl.span.p, ph.span.data(), ph.span.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+               (e = cudaMemset(pl.counters.p, 0, pl.counters.bytes)) != cudaSuccess) {
         return cuda_fail(e, "plan upload");
+    }
     pl.K = t.K;
     pl.kslabs = t.kslabs;
     pl.Tc = t.Tc;
@@ -476,11 +582,13 @@ static pe_status create_poly_device(const pe_poly_desc *d, int variant, pe_poly 
         stage_release(stg);
     };
     cudaError_t e;
-    if ((e = P->coeffs.ensure(cbytes, us)) != cudaSuccess || (!dev_in && (e = raw.ensure(ebytes, us)) != cudaSuccess) ||
-        (e = keys.ensure(s * 8, us)) != cudaSuccess || (e = counts.ensure(nb * 8, us)) != cudaSuccess ||
-        (e = base.ensure((nb + 1) * 8, us)) != cudaSuccess || (e = goff.ensure(s * 8, us)) != cudaSuccess ||
-        (e = gkeys.ensure(s * 8, us)) != cudaSuccess || (e = info.ensure(sizeof(CreateInfo), us)) != cudaSuccess ||
-        (e = P->mR.ensure(s * 8, us)) != cudaSuccess) {
+    if ((e = P->coeffs.ensure_async(cbytes, us)) != cudaSuccess ||
+        (!dev_in && (e = raw.ensure_async(ebytes, us)) != cudaSuccess) ||
+        (e = keys.ensure_async(s * 8, us)) != cudaSuccess || (e = counts.ensure_async(nb * 8, us)) != cudaSuccess ||
+        (e = base.ensure_async((nb + 1) * 8, us)) != cudaSuccess || (e = goff.ensure_async(s * 8, us)) != cudaSuccess ||
+        (e = gkeys.ensure_async(s * 8, us)) != cudaSuccess ||
+        (e = info.ensure_async(sizeof(CreateInfo), us)) != cudaSuccess ||
+        (e = P->mR.ensure_async(s * 8, us)) != cudaSuccess) {
         finish();
         return cuda_fail(e, "device allocation");
     }
@@ -493,20 +601,14 @@ static pe_status create_poly_device(const pe_poly_desc *d, int variant, pe_poly 
             return PE_OK;
         }
         unsigned char *dst = (unsigned char *)stg.p;
-        const unsigned nth = host_threads ? std::max(1u, std::min(16u, std::thread::hardware_concurrency())) : 1u;
-        auto copy = [&](unsigned t) {
+        const unsigned nth = host_threads ? 2 * host_pool_size() : 1u;
+        const std::function<void(unsigned)> copy = [&](unsigned t) {
             const size_t c0 = cbytes * t / nth, c1 = cbytes * (t + 1) / nth;
             const size_t e0 = ebytes * t / nth, e1 = ebytes * (t + 1) / nth;
             memcpy(dst + c0, (const unsigned char *)d->coeffs + c0, c1 - c0);
             memcpy(dst + cbytes + e0, (const unsigned char *)d->exps + e0, e1 - e0);
         };
-        if (nth == 1) {
-            copy(0);
-        } else {
-            std::vector<std::thread> th;
-            for (unsigned t = 0; t < nth; ++t) th.emplace_back(copy, t);
-            for (std::thread &x : th) x.join();
-        }
+        host_parallel(nth, copy);
         if ((e = cudaMemcpyAsync(P->coeffs.p, dst, cbytes, cudaMemcpyHostToDevice, us)) != cudaSuccess ||
             (e = cudaMemcpyAsync(raw.p, dst + cbytes, ebytes, cudaMemcpyHostToDevice, us)) != cudaSuccess) {
             finish();
@@ -563,8 +665,8 @@ static pe_status create_poly_device(const pe_poly_desc *d, int variant, pe_poly 
     P->group_off.resize(G + 1);
     P->keys.resize(2 * G);
     const size_t dp1 = ci.dmax + 1;
-    if ((e = P->exps.ensure((size_t)E * s * P->exp_bytes, us)) != cudaSuccess ||
-        (e = P->ptab.ensure((size_t)E * dp1 * 8, us)) != cudaSuccess ||
+    if ((e = P->exps.ensure_async((size_t)E * s * P->exp_bytes, us)) != cudaSuccess ||
+        (e = P->ptab.ensure_async((size_t)E * dp1 * 8, us)) != cudaSuccess ||
         (e = cudaMemcpyAsync(P->group_off.data(), goff.p, G * 8, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
         (e = cudaMemcpyAsync(P->keys.data(), gkeys.p, 2 * G * 4, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
         (e = launch_pack_exps(dexps, w, s, n, P->exp_bytes, P->exps.p, us)) != cudaSuccess ||
@@ -671,13 +773,11 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
         t_sorted[t] = srt;
     };
     auto parallel = [&](auto fn) {
-        if (nth == 1) {
-            fn(0u);
-            return;
-        }
-        std::vector<std::thread> th;
-        for (unsigned t = 0; t < nth; ++t) th.emplace_back(fn, t);
-        for (std::thread &x : th) x.join();
+        const std::function<void(unsigned)> f = fn;
+        if (nth == 1)
+            f(0u);
+        else
+            host_parallel(nth, f);
     };
     parallel(scan);
     uint32_t dmax = 0;
@@ -816,7 +916,7 @@ extern "C" pe_status poly_eval_set_tiles(pe_poly *P, const pe_tiles *t)
     return PE_OK;
 }
 
-static pe_status plan_for(pe_poly *P, uint64_t T, Tiles *tiles)
+static pe_status plan_for(pe_poly *P, uint64_t T, Tiles *tiles, cudaStream_t st = nullptr, bool queued = false)
 {
     const int v = run_variant(P, T);
     if (v != P->variant) {
@@ -830,12 +930,12 @@ static pe_status plan_for(pe_poly *P, uint64_t T, Tiles *tiles)
         P->tail_plan.valid = false;
         P->tailT = tiles->tailT;
     }
-    pe_status st = ensure_plan(P, P->plan, *tiles, T - tiles->tailT);
-    if (st != PE_OK || !tiles->tailT) return st;
+    pe_status ps = ensure_plan(P, P->plan, *tiles, T - tiles->tailT, st, queued);
+    if (ps != PE_OK || !tiles->tailT) return ps;
     Tiles tt = *tiles;
     tt.kslabs = 1;
     tt.Tc = tail_tc(tiles->tailT);
-    return ensure_plan(P, P->tail_plan, tt, tiles->tailT);
+    return ensure_plan(P, P->tail_plan, tt, tiles->tailT, st, queued);
 }
 
 extern "C" pe_status poly_eval_plan_info(pe_poly *P, uint64_t T, pe_plan_info *info)
@@ -938,7 +1038,7 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
         cudaStreamWaitEvent(alloc_stream(), P->last_use, 0);
     }
     Tiles t;
-    if ((st = plan_for(P, T, &t)) != PE_OK) return st;
+    if ((st = plan_for(P, T, &t, cs, true)) != PE_OK) return st;
     cudaPointerAttributes attr{};
     bool dev_out = false;
     if (cudaPointerGetAttributes(&attr, out) == cudaSuccess)
@@ -947,7 +1047,7 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
     uint64_t *out_dev = out;
     cudaError_t e;
     if (!dev_out) {
-        if ((e = P->out_scratch.ensure(T * P->G * 8)) != cudaSuccess) return cuda_fail(e, "output scratch");
+        if ((e = P->out_scratch.ensure_async(T * P->G * 8, cs)) != cudaSuccess) return cuda_fail(e, "output scratch");
         out_dev = P->out_scratch.as<uint64_t>();
     }
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -976,7 +1076,7 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
     if (use_starts) {
         for (uint32_t q = 0; q < q0; ++q) sr.row[sr.n++] = q * P->plan.Tc;
         for (uint32_t q = 0; q < q1; ++q) sr.row[sr.n++] = (uint32_t)T0 + q * P->tail_plan.Tc;
-        if ((e = P->vstart.ensure((size_t)sr.n * P->s * 8)) != cudaSuccess) return cuda_fail(e, "start values");
+        if ((e = P->vstart.ensure_async((size_t)sr.n * P->s * 8, cs)) != cudaSuccess) return cuda_fail(e, "start values");
         e = launch_stepA_starts(P->exps.p, P->exp_bytes, P->coeffs.as<uint64_t>(), P->s, P->E,
                                 P->ptab.as<uint64_t>(), dp1, P->mc, t0, sr, P->mR.as<uint64_t>(),
                                 P->vstart.as<uint64_t>(), num_sms(), cs);

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 #include <cuda_runtime.h>
@@ -52,9 +53,29 @@ struct DevBuf {
         bytes = n;
         return cudaSuccess;
     }
+    // The same without waiting: the buffer is usable by work queued on `s`
+    // (and by other streams once they wait for that work).
+    cudaError_t ensure_async(size_t n, cudaStream_t s)
+    {
+        if (n <= bytes && p) return cudaSuccess;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMallocAsync(&p, n, s);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n;
+        return cudaSuccess;
+    }
     template <typename T>
     T *as() const { return reinterpret_cast<T *>(p); }
 };
+
+// Runs fn(0) .. fn(n-1) on a persistent pool of host threads (the caller
+// takes part); calls from several host threads take turns.
+void host_parallel(unsigned n, const std::function<void(unsigned)> &fn);
+unsigned host_pool_size();
 
 // Host side of a Step B work decomposition: units of kslabs slabs, T-chunks
 // of Tc points, and the groups that cross unit boundaries ("spans").
@@ -153,7 +174,11 @@ int num_sms();
 // Chooses the tile shape for a run of T points (forced fields win).
 Tiles choose_tiles(pe_poly *poly, uint64_t T, const pe_tiles *forced);
 // Builds (or reuses) `pl` for the given tiles and T.
-pe_status ensure_plan(pe_poly *poly, Plan &pl, const Tiles &t, uint64_t T);
+// With `queued`, allocations, uploads and the counter reset are queued on
+// `st` (the plan is then valid for work queued after them on that stream);
+// otherwise they complete before the call returns.
+pe_status ensure_plan(pe_poly *poly, Plan &pl, const Tiles &t, uint64_t T, cudaStream_t st = nullptr,
+                      bool queued = false);
 void build_chunks(pe_poly *P, uint32_t K);
 void build_plan_host(pe_poly *P, const Tiles &t, uint64_t T, PlanHost &ph);
 void fill_job(StepBJob &J, pe_poly *P, const PlanHost &ph, const uint32_t *cs, const uint32_t *cg,
