@@ -169,6 +169,47 @@ def cpu_baseline(w, stride):
             "seconds": dt}
 
 
+def _oracle_share(config, rank, nproc, barrier, queue):
+    """Child of cpu_baseline_all_cores: Algorithm 1 of the oracle on the groups
+    g with g % nproc == rank, all T points, timed after a common barrier."""
+    import oracle
+    w = make_workload(config)
+    _, tg = oracle.group_keys(w.exps)
+    sel = (tg % nproc) == rank
+    sub = wl.Workload(p=w.p, n=w.n, coeffs=w.coeffs[sel], exps=w.exps[sel], beta=w.beta, T=w.T, t0=w.t0)
+    oracle.build()
+    barrier.wait()
+    t = time.perf_counter()
+    oracle.eval_matrix(sub)
+    queue.put((sub.term_points, time.perf_counter() - t))
+
+
+def cpu_baseline_all_cores(config, nproc=None):
+    """The same oracle as independent processes over disjoint group subsets of
+    the full workload, one per host core (spawned, not forked)."""
+    import multiprocessing as mp
+    nproc = nproc or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(nproc), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_share, args=(config, r, nproc, barrier, queue)) for r in range(nproc)]
+    for pr in procs:
+        pr.start()
+    try:
+        res = [queue.get(timeout=600) for _ in procs]
+    except Exception as ex:  # a child failed: report it instead of waiting
+        for pr in procs:
+            pr.terminate()
+        return {"error": f"oracle processes did not finish: {ex!r}"}
+    for pr in procs:
+        pr.join()
+    tp = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return {"value": tp / dt, "unit": "term-points/s", "cores": nproc, "kind": "oracle",
+            "sample": f"Algorithm 1 of the oracle (gcc -O2) as {nproc} processes over disjoint group subsets "
+                      f"(g mod {nproc}) of the full workload: {tp:.3e} term-points, slowest process {dt:.2f} s",
+            "seconds": dt}
+
+
 def hbm_peak_gbs():
     """Measured copy bandwidth of this machine's GPUs, else the stated fallback."""
     try:
@@ -417,6 +458,8 @@ def run_ours(args):
             "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_stride)
+        if args.config in ("large", "large30", "tiny"):
+            line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.config)
     if world == 1 and not args.no_extras:
         line["sparse_images"] = bench_compact(pe, out, torch)
         line["interpolation"] = bench_interp(pe, torch, mhz)
