@@ -125,6 +125,20 @@ typedef struct pe_poly pe_poly;
 pe_status poly_eval_create(const pe_poly_desc *desc, pe_poly **out);
 
 /*
+ * The same terms modulo another prime (multi-prime evaluation for Chinese
+ * remaindering, the smaller primes of the paper's concluding remarks): a new
+ * handle that shares `layout`'s exponents, groups and term order on the
+ * device and owns only its coefficients.  `coeffs` holds the s coefficients
+ * reduced mod p, in the order of the terms given to poly_eval_create for
+ * `layout` (host, or device with PE_FLAG_DEVICE_PTRS in `flags`).  The shared
+ * exponents live until the last handle that uses them is destroyed, so
+ * `layout` may be destroyed first.
+ * Errors: PE_ERR_ARG, PE_ERR_PRIME, PE_ERR_NOT_REDUCED, PE_ERR_NOMEM, PE_ERR_CUDA.
+ */
+pe_status poly_eval_create_like(const pe_poly *layout, uint64_t p, const uint64_t *coeffs, uint32_t flags,
+                                pe_variant variant, pe_poly **out);
+
+/*
  * Number of nonempty (x1, x2) groups G and, if keys != NULL, their (d, e)
  * pairs in column order: keys[2g] = d, keys[2g+1] = e (host array of 2G).
  */

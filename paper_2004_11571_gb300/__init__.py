@@ -140,6 +140,7 @@ def lib():
             "poly_eval_int_pipe_rates": (st, [ctypes.POINTER(ctypes.c_double)]),
             "poly_eval_compact": (st, [_vp, _u64, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
             "poly_eval_monomials": (st, [_vp, _vp, _vp, _vp, _vp]),
+            "poly_eval_create_like": (st, [_vp, _u64, _vp, _u32, ctypes.c_int, ctypes.POINTER(_vp)]),
             "poly_eval_vandermonde_solve": (st, [_u64, _u64, _vp, _vp, _vp, _u64, _u64, _u64, _vp, _vp]),
             "poly_eval_vandermonde_timing": (st, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         }
@@ -223,6 +224,21 @@ class Poly:
     @classmethod
     def from_workload(cls, w, variant="auto"):
         return cls(w.p, w.coeffs, w.exps, variant=variant)
+
+    def like(self, p: int, coeffs, variant="auto"):
+        """The same terms modulo another prime p (coefficients reduced mod p, in
+        the order given to this polynomial's constructor); shares the device
+        exponents (poly_eval_create_like)."""
+        if _is_torch(coeffs):
+            ptr, flags, keep = coeffs.data_ptr(), FLAG_DEVICE_PTRS, coeffs
+        else:
+            keep = np.ascontiguousarray(np.asarray(coeffs, dtype=np.uint64).reshape(-1))
+            ptr, flags = keep.ctypes.data, 0
+        h = ctypes.c_void_p()
+        _check(lib().poly_eval_create_like(self._h, int(p), ptr, flags, _variant(variant), ctypes.byref(h)))
+        q = Poly.__new__(Poly)
+        q._h, q.p, q.n, q.s, q.G = h, int(p), self.n, self.s, self.G
+        return q
 
     @property
     def handle(self):

@@ -435,7 +435,7 @@ void fill_job(StepBJob &J, pe_poly *P, const PlanHost &ph, const uint32_t *cs, c
     J = StepBJob{};
     J.coeffs = P->coeffs.as<uint64_t>();
     J.mR = mR;
-    J.exps = P->exps.p;
+    J.exps = P->exps->p;
     J.ptab = ptab;
     J.cs = cs;
     J.cg = cg;
@@ -665,11 +665,11 @@ static pe_status create_poly_device(const pe_poly_desc *d, int variant, pe_poly 
     P->group_off.resize(G + 1);
     P->keys.resize(2 * G);
     const size_t dp1 = ci.dmax + 1;
-    if ((e = P->exps.ensure_async((size_t)E * s * P->exp_bytes, us)) != cudaSuccess ||
+    if ((e = P->exps->ensure_async((size_t)E * s * P->exp_bytes, us)) != cudaSuccess ||
         (e = P->ptab.ensure_async((size_t)E * dp1 * 8, us)) != cudaSuccess ||
         (e = cudaMemcpyAsync(P->group_off.data(), goff.p, G * 8, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
         (e = cudaMemcpyAsync(P->keys.data(), gkeys.p, 2 * G * 4, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
-        (e = launch_pack_exps(dexps, w, s, n, P->exp_bytes, P->exps.p, us)) != cudaSuccess ||
+        (e = launch_pack_exps(dexps, w, s, n, P->exp_bytes, P->exps->p, us)) != cudaSuccess ||
         (e = cudaStreamSynchronize(us)) != cudaSuccess) {
         finish();
         return cuda_fail(e, "packing terms");
@@ -853,7 +853,7 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
     cudaError_t e;
     const size_t dp1 = dmax + 1;
     cudaStream_t us = upload_stream_acquire();
-    if ((e = P->coeffs.ensure(s * 8, us)) != cudaSuccess || (e = P->exps.ensure(se_bytes, us)) != cudaSuccess ||
+    if ((e = P->coeffs.ensure(s * 8, us)) != cudaSuccess || (e = P->exps->ensure(se_bytes, us)) != cudaSuccess ||
         (e = P->mR.ensure(s * 8, us)) != cudaSuccess || (e = P->ptab.ensure((size_t)E * dp1 * 8, us)) != cudaSuccess) {
         upload_stream_release(us);
         stage_release(stg);
@@ -861,7 +861,7 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
         return cuda_fail(e, "device allocation");
     }
     if ((s && (e = cudaMemcpyAsync(P->coeffs.p, sc, s * 8, cudaMemcpyHostToDevice, us)) != cudaSuccess) ||
-        (se_bytes && (e = cudaMemcpyAsync(P->exps.p, se, se_bytes, cudaMemcpyHostToDevice, us)) != cudaSuccess) ||
+        (se_bytes && (e = cudaMemcpyAsync(P->exps->p, se, se_bytes, cudaMemcpyHostToDevice, us)) != cudaSuccess) ||
         (e = cudaStreamSynchronize(us)) != cudaSuccess) {
         upload_stream_release(us);
         stage_release(stg);
@@ -870,7 +870,85 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
     }
     upload_stream_release(us);
     stage_release(stg);
+    if (!sorted) P->perm = std::make_shared<const std::vector<uint32_t>>(std::move(perm));
     *out = P;
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_create_like(const pe_poly *L, uint64_t p, const uint64_t *coeffs, uint32_t flags,
+                                           pe_variant variant, pe_poly **out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return PE_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!L || (L->s && !coeffs)) {
+        set_error("layout or coeffs is NULL");
+        return PE_ERR_ARG;
+    }
+    if (variant != PE_MODMUL_AUTO && variant != PE_MODMUL_MONT64 && variant != PE_MODMUL_FP64 &&
+        variant != PE_MODMUL_BARRETT64 && variant != PE_MODMUL_BARRETT32) {
+        set_error("unknown variant %d", (int)variant);
+        return PE_ERR_ARG;
+    }
+    pe_status st = check_prime(p, variant);
+    if (st != PE_OK) return st;
+    const uint64_t s = L->s;
+    // Coefficients in the caller's order, on the host.
+    std::vector<uint64_t> hc;
+    const uint64_t *c = coeffs;
+    cudaError_t e;
+    if ((flags & PE_FLAG_DEVICE_PTRS) && s) {
+        hc.resize(s);
+        if ((e = cudaMemcpy(hc.data(), coeffs, s * 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "reading device coefficients");
+        c = hc.data();
+    }
+    for (uint64_t i = 0; i < s; ++i)
+        if (c[i] >= p) {
+            set_error("coefficient %llu of term %llu is not reduced mod p", (unsigned long long)c[i],
+                      (unsigned long long)i);
+            return PE_ERR_NOT_REDUCED;
+        }
+    std::unique_ptr<pe_poly> P(new pe_poly());
+    P->p = p;
+    P->n = L->n;
+    P->E = L->E;
+    P->s = s;
+    P->G = L->G;
+    P->requested_variant = variant;
+    P->variant = variant == PE_MODMUL_AUTO ? default_variant(p) : variant;
+    P->mc = make_modctx(p);
+    P->exp_bytes = L->exp_bytes;
+    P->dmax = L->dmax;
+    P->group_off = L->group_off;
+    P->keys = L->keys;
+    P->exps = L->exps;
+    P->perm = L->perm;
+    Staging stg = stage_acquire(std::max<uint64_t>(s, 1) * 8);
+    std::vector<uint64_t> fallback;
+    if (!stg.p) fallback.resize(std::max<uint64_t>(s, 1));
+    uint64_t *sc = stg.p ? (uint64_t *)stg.p : fallback.data();
+    if (P->perm)
+        for (uint64_t i = 0; i < s; ++i) sc[i] = c[(*P->perm)[i]];
+    else
+        memcpy(sc, c, s * 8);
+    cudaStream_t us = upload_stream_acquire();
+    const size_t dp1 = P->dmax + 1;
+    if ((e = P->coeffs.ensure_async(s * 8, us)) != cudaSuccess || (e = P->mR.ensure_async(s * 8, us)) != cudaSuccess ||
+        (e = P->ptab.ensure_async((size_t)P->E * dp1 * 8, us)) != cudaSuccess ||
+        (s && (e = cudaMemcpyAsync(P->coeffs.p, sc, s * 8, cudaMemcpyHostToDevice, us)) != cudaSuccess)) {
+        cudaStreamSynchronize(us);
+        upload_stream_release(us);
+        stage_release(stg);
+        return cuda_fail(e, "uploading coefficients");
+    }
+    e = cudaStreamSynchronize(us);
+    upload_stream_release(us);
+    stage_release(stg);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading coefficients");
+    *out = P.release();
     return PE_OK;
 }
 
@@ -1077,11 +1155,11 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
         for (uint32_t q = 0; q < q0; ++q) sr.row[sr.n++] = q * P->plan.Tc;
         for (uint32_t q = 0; q < q1; ++q) sr.row[sr.n++] = (uint32_t)T0 + q * P->tail_plan.Tc;
         if ((e = P->vstart.ensure_async((size_t)sr.n * P->s * 8, cs)) != cudaSuccess) return cuda_fail(e, "start values");
-        e = launch_stepA_starts(P->exps.p, P->exp_bytes, P->coeffs.as<uint64_t>(), P->s, P->E,
+        e = launch_stepA_starts(P->exps->p, P->exp_bytes, P->coeffs.as<uint64_t>(), P->s, P->E,
                                 P->ptab.as<uint64_t>(), dp1, P->mc, t0, sr, P->mR.as<uint64_t>(),
                                 P->vstart.as<uint64_t>(), num_sms(), cs);
     } else {
-        e = launch_stepA(P->exps.p, P->exp_bytes, P->s, P->E, P->ptab.as<uint64_t>(), dp1, P->mc,
+        e = launch_stepA(P->exps->p, P->exp_bytes, P->s, P->E, P->ptab.as<uint64_t>(), dp1, P->mc,
                          P->mR.as<uint64_t>(), num_sms(), cs);
     }
     if (e != cudaSuccess) return cuda_fail(e, "Step A");

@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cstring>
 #include <functional>
+#include <memory>
 #include <string>
 #include <vector>
 #include <cuda_runtime.h>
@@ -146,7 +147,12 @@ struct pe_poly {
     uint32_t dmax = 0;           // max exponent over x3..xn
     std::vector<uint64_t> group_off;   // G+1 (host)
     std::vector<uint32_t> keys;        // 2G (host)
-    pe::DevBuf coeffs, exps, mR, ptab, out_scratch, vstart;
+    pe::DevBuf coeffs, mR, ptab, out_scratch, vstart;
+    // Exponents of x3..xn (E rows of s), shared with the polynomials made by
+    // poly_eval_create_like, and the permutation that put the input terms in
+    // group order (empty when they already were).
+    std::shared_ptr<pe::DevBuf> exps = std::make_shared<pe::DevBuf>();
+    std::shared_ptr<const std::vector<uint32_t>> perm;
     pe::HostChunks chunks;
     pe::Plan plan;        // band of large items: rows [0, T - tail)
     pe::Plan tail_plan;   // band of small items: the last tail rows
@@ -163,7 +169,7 @@ struct pe_poly {
     }
     uint64_t device_bytes() const
     {
-        return coeffs.bytes + exps.bytes + mR.bytes + ptab.bytes + out_scratch.bytes + vstart.bytes + plan.cs.bytes +
+        return coeffs.bytes + (exps.use_count() == 1 ? exps->bytes : 0) + mR.bytes + ptab.bytes + out_scratch.bytes + vstart.bytes + plan.cs.bytes +
                plan.cg.bytes + plan.unit.bytes + plan.span.bytes + plan.scratch_bytes() + tail_plan.cs.bytes +
                tail_plan.cg.bytes + tail_plan.unit.bytes + tail_plan.span.bytes + tail_plan.scratch_bytes();
     }

@@ -524,7 +524,7 @@ extern "C" pe_status poly_eval_monomials(pe_poly *P, const uint64_t *beta, uint6
         (e = P->mR.ensure(P->s * 8)) != cudaSuccess)
         return cuda_fail(e, "monomial scratch");
     if ((e = launch_powtab(barg, P->E, dp1, P->mc, P->ptab.as<uint64_t>(), cs)) != cudaSuccess ||
-        (e = launch_stepA(P->exps.p, P->exp_bytes, P->s, P->E, P->ptab.as<uint64_t>(), dp1, P->mc,
+        (e = launch_stepA(P->exps->p, P->exp_bytes, P->s, P->E, P->ptab.as<uint64_t>(), dp1, P->mc,
                           P->mR.as<uint64_t>(), num_sms(), cs)) != cudaSuccess)
         return cuda_fail(e, "Step A");
     const unsigned grid = (unsigned)std::min<uint64_t>((P->s + 255) / 256, (uint64_t)num_sms() * 8);
