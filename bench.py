@@ -239,6 +239,55 @@ def bench_compact(pe, dense, torch, reps=20):
             "note": "host-timed, includes one stream synchronization per call"}
 
 
+def bench_multiprime(pe, torch, w, nprimes=4, reps=5):
+    """The benchmark's term list modulo several 62-bit primes (Chinese
+    remaindering): one full create, then poly_eval_create_like per extra prime
+    (coefficients only), and all primes evaluated in one batch."""
+    primes = [int(w.p)] + [wl.random_prime(62, 7000 + k) for k in range(1, nprimes)]
+    ints = np.random.default_rng(7).integers(0, 1 << 63, size=w.s, dtype=np.uint64)
+    coeffs = [(ints % np.uint64(p)).astype(np.uint64) for p in primes]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    layout = pe.Poly(primes[0], coeffs[0], w.exps, sorted_hint=True)
+    create_ms = (time.perf_counter() - t) * 1e3
+    t = time.perf_counter()
+    polys = [layout] + [layout.like(p, c) for p, c in zip(primes[1:], coeffs[1:])]
+    like_ms = (time.perf_counter() - t) * 1e3 / (nprimes - 1)
+    outs = [torch.empty((w.T, layout.G), dtype=torch.int64, device="cuda") for _ in primes]
+    betas = [np.random.default_rng(100 + k).integers(2, p, size=w.n - 2, dtype=np.uint64)
+             for k, p in enumerate(primes)]
+    batch = pe.Batch([(q, b, w.T, 1, o) for q, b, o in zip(polys, betas, outs)])
+    for _ in range(2):
+        batch.launch()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(reps):
+        batch.launch()
+    ev[1].record()
+    torch.cuda.synchronize()
+    batch_ms = ev[0].elapsed_time(ev[1]) / reps
+    for q, b, o in zip(polys, betas, outs):
+        q.run(b, w.T, out=o)
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(reps):
+        for q, b, o in zip(polys, betas, outs):
+            q.run(b, w.T, out=o)
+    ev[1].record()
+    torch.cuda.synchronize()
+    loop_ms = ev[0].elapsed_time(ev[1]) / reps
+    batch.close()
+    for q in polys:
+        q.close()
+    tp = nprimes * w.s * w.T
+    return {"primes": nprimes, "create_ms": create_ms, "create_like_ms": like_ms,
+            "shared_exponent_bytes": int(w.s * (w.n - 2)), "batch_ms": batch_ms,
+            "batch_term_points_per_s": tp / (batch_ms * 1e-3), "loop_ms": loop_ms,
+            "loop_term_points_per_s": tp / (loop_ms * 1e-3),
+            "note": "create/create_like host-timed; batch and loop timed with CUDA events, inputs resident"}
+
+
 def _vdm_counts(off):
     """Algorithmic multiplies of the solver: exact 64x64-bit products of the
     product tree and of the correlation, fixed-multiplier products of Horner."""
@@ -463,6 +512,8 @@ def run_ours(args):
     if world == 1 and not args.no_extras:
         line["sparse_images"] = bench_compact(pe, out, torch)
         line["interpolation"] = bench_interp(pe, torch, mhz)
+        if args.config == "large":
+            line["multi_prime"] = bench_multiprime(pe, torch, w)
     poly.close()
     if world == 1 and not args.no_extras:
         del out, flush

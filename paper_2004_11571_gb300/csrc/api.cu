@@ -905,12 +905,33 @@ extern "C" pe_status poly_eval_create_like(const pe_poly *L, uint64_t p, const u
             return cuda_fail(e, "reading device coefficients");
         c = hc.data();
     }
-    for (uint64_t i = 0; i < s; ++i)
-        if (c[i] >= p) {
-            set_error("coefficient %llu of term %llu is not reduced mod p", (unsigned long long)c[i],
-                      (unsigned long long)i);
-            return PE_ERR_NOT_REDUCED;
+    // Range check and copy into staging (in group order), split over the host pool.
+    Staging stg = stage_acquire(std::max<uint64_t>(s, 1) * 8);
+    std::vector<uint64_t> fallback;
+    if (!stg.p) fallback.resize(std::max<uint64_t>(s, 1));
+    uint64_t *sc = stg.p ? (uint64_t *)stg.p : fallback.data();
+    const std::vector<uint32_t> *perm = L->perm.get();
+    const unsigned nth = s >= (1u << 16) ? 2 * host_pool_size() : 1u;
+    std::vector<uint64_t> t_bad(nth, ~0ull);
+    const std::function<void(unsigned)> fill = [&](unsigned t) {
+        const uint64_t i0 = s * t / nth, i1 = s * (t + 1) / nth;
+        uint64_t bad = ~0ull;
+        for (uint64_t i = i0; i < i1; ++i) {
+            const uint64_t v = c[perm ? (*perm)[i] : i];
+            if (v >= p && bad == ~0ull) bad = perm ? (*perm)[i] : i;
+            sc[i] = v;
         }
+        t_bad[t] = bad;
+    };
+    host_parallel(nth, fill);
+    uint64_t bad = ~0ull;
+    for (uint64_t b : t_bad) bad = std::min(bad, b);
+    if (bad != ~0ull) {
+        stage_release(stg);
+        set_error("coefficient %llu of term %llu is not reduced mod p", (unsigned long long)c[bad],
+                  (unsigned long long)bad);
+        return PE_ERR_NOT_REDUCED;
+    }
     std::unique_ptr<pe_poly> P(new pe_poly());
     P->p = p;
     P->n = L->n;
@@ -926,14 +947,6 @@ extern "C" pe_status poly_eval_create_like(const pe_poly *L, uint64_t p, const u
     P->keys = L->keys;
     P->exps = L->exps;
     P->perm = L->perm;
-    Staging stg = stage_acquire(std::max<uint64_t>(s, 1) * 8);
-    std::vector<uint64_t> fallback;
-    if (!stg.p) fallback.resize(std::max<uint64_t>(s, 1));
-    uint64_t *sc = stg.p ? (uint64_t *)stg.p : fallback.data();
-    if (P->perm)
-        for (uint64_t i = 0; i < s; ++i) sc[i] = c[(*P->perm)[i]];
-    else
-        memcpy(sc, c, s * 8);
     cudaStream_t us = upload_stream_acquire();
     const size_t dp1 = P->dmax + 1;
     if ((e = P->coeffs.ensure_async(s * 8, us)) != cudaSuccess || (e = P->mR.ensure_async(s * 8, us)) != cudaSuccess ||
