@@ -162,6 +162,19 @@ pe_status poly_eval_groups(const pe_poly *poly, uint64_t *G, uint32_t *keys);
 pe_status poly_eval_run(pe_poly *poly, const uint64_t *beta, uint64_t T, uint64_t t0,
                         uint64_t *out, void *stream);
 
+/*
+ * The same images by the asymptotically fast method (Sect. 2.3.1): for each
+ * group, sum_t b_(t0+t) z^t = N(z)/D(z) with D = prod (1 - m_i z), from a
+ * product tree of NTT polynomial products and a Newton inversion of D, in
+ * O(s log^2 T) products instead of s*T.  Needs an NTT-friendly prime: p - 1
+ * divisible by 2*Tp, Tp = T rounded up to a power of two (at least 64); and
+ * T <= 4096.  Arguments, layout and ordering as poly_eval_run; the result is
+ * identical.  Errors: PE_ERR_ARG, PE_ERR_PRIME (p - 1 lacks the power of
+ * two), PE_ERR_NOMEM, PE_ERR_CUDA.
+ */
+pe_status poly_eval_run_fast(pe_poly *poly, const uint64_t *beta, uint64_t T, uint64_t t0, uint64_t *out,
+                             void *stream);
+
 /* Waits for the device to finish queued work (like cudaFree), then frees the
  * handle and returns its device memory to the library's pool (NULL: no-op). */
 void poly_eval_destroy(pe_poly *poly);

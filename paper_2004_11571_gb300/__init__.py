@@ -141,6 +141,7 @@ def lib():
             "poly_eval_compact": (st, [_vp, _u64, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
             "poly_eval_monomials": (st, [_vp, _vp, _vp, _vp, _vp]),
             "poly_eval_create_like": (st, [_vp, _u64, _vp, _u32, ctypes.c_int, ctypes.POINTER(_vp)]),
+            "poly_eval_run_fast": (st, [_vp, _vp, _u64, _u64, _vp, _vp]),
             "poly_eval_vandermonde_solve": (st, [_u64, _u64, _vp, _vp, _vp, _u64, _u64, _u64, _vp, _vp]),
             "poly_eval_vandermonde_timing": (st, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         }
@@ -272,6 +273,17 @@ class Poly:
         _check(lib().poly_eval_monomials(self._h, b.ctypes.data if b.size else None, z.data_ptr(),
                                          off.ctypes.data, _stream_ptr(stream)))
         return z[: self.s], off
+
+    def run_fast(self, beta: Sequence[int], T: int, t0: int = 1, out=None, stream=None):
+        """The same images by the fast method (poly_eval_run_fast; NTT-friendly p, T <= 4096)."""
+        b = np.ascontiguousarray(np.asarray(beta, dtype=np.uint64).reshape(-1))
+        if out is None:
+            import torch
+            out = torch.empty((int(T), self.G), dtype=torch.int64, device="cuda")
+        ptr = out.data_ptr() if _is_torch(out) else out.ctypes.data
+        _check(lib().poly_eval_run_fast(self._h, b.ctypes.data if b.size else None, int(T), int(t0), ptr,
+                                        _stream_ptr(stream)))
+        return out
 
     def set_tiles(self, K=0, slabs=0, tchunk=0, warps_per_block=0, tail=0):
         t = _Tiles(K, slabs, tchunk, warps_per_block, tail)

@@ -136,6 +136,9 @@ cudaError_t batch_enqueue(const BatchImage &img, cudaStream_t st);
 
 }  // namespace pe
 
+struct FastPlan;
+void fast_plan_delete(FastPlan *f);
+
 struct pe_poly {
     uint64_t p = 0;
     uint32_t n = 0, E = 0;
@@ -153,6 +156,7 @@ struct pe_poly {
     // group order (empty when they already were).
     std::shared_ptr<pe::DevBuf> exps = std::make_shared<pe::DevBuf>();
     std::shared_ptr<const std::vector<uint32_t>> perm;
+    std::unique_ptr<FastPlan, void (*)(FastPlan *)> fast{nullptr, fast_plan_delete};   // poly_eval_run_fast state
     pe::HostChunks chunks;
     pe::Plan plan;        // band of large items: rows [0, T - tail)
     pe::Plan tail_plan;   // band of small items: the last tail rows

@@ -55,29 +55,6 @@ struct VdmTile {
     uint64_t pbase;   // partial of chunk kappa, output j: part[pbase + kappa * n + j]
 };
 
-// (h, m, l) += a * b, exact (a, b < 2^64, h counts the carries out of 128 bits).
-__device__ __forceinline__ void mac192(uint64_t &l, uint64_t &m, uint32_t &h, uint64_t a, uint64_t b)
-{
-    asm("mad.lo.cc.u64 %0, %3, %4, %0;\n\t"
-        "madc.hi.cc.u64 %1, %3, %4, %1;\n\t"
-        "addc.u32 %2, %2, 0;"
-        : "+l"(l), "+l"(m), "+r"(h)
-        : "l"(a), "l"(b));
-}
-
-// (h*2^128 + m*2^64 + l) mod p, canonical, for h < p (the sums below stay far
-// under p * 2^128).  With R = 2^64: REDC(l) = l/R, REDC((h, m + l/R)) =
-// h + m/R + l/R^2 = x/R^2, and a Montgomery product by R^3 gives x.
-__device__ __forceinline__ uint64_t reduce192(uint64_t l, uint64_t m, uint32_t h, uint64_t r3, const ModCtx &mc)
-{
-    const uint64_t a = mont_redc(l, 0, mc);
-    uint64_t lo;
-    uint32_t hi = h;
-    asm("add.cc.u64 %0, %2, %3;\n\taddc.u32 %1, %1, 0;" : "=l"(lo), "+r"(hi) : "l"(m), "l"(a));
-    const uint64_t b = mont_redc(lo, hi, mc);
-    return canon(mont_mul(b, r3, mc), mc.p);
-}
-
 // x in [0, 3p) to [0, p).
 __device__ __forceinline__ uint64_t canon3(uint64_t x, const ModCtx &mc)
 {

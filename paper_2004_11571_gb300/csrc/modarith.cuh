@@ -124,6 +124,33 @@ __device__ __forceinline__ uint64_t reduce96(uint64_t lo, uint32_t hi, const Mod
     return s >= mc.p ? s - mc.p : s;
 }
 
+// ------------------------------------------------ 192-bit exact sums
+// (h, m, l) += a * b, exact (a, b < 2^64, h counts the carries out of 128 bits).
+__device__ __forceinline__ void mac192(uint64_t &l, uint64_t &m, uint32_t &h, uint64_t a, uint64_t b)
+{
+    asm("mad.lo.cc.u64 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u64 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+l"(l), "+l"(m), "+r"(h)
+        : "l"(a), "l"(b));
+}
+
+// x = h*2^128 + m*2^64 + l times fac/R^3 mod p, canonical, for h < p (sums of
+// fewer than 2^64 products of values below 2^62 stay far under p * 2^128).
+// With R = 2^64: REDC(l) = l/R, REDC((h, m + l/R)) = h + m/R + l/R^2 = x/R^2,
+// and a Montgomery product by fac gives x fac / R^3: fac = R^3 mod p yields
+// x mod p, fac = R^2 mod p yields x/R (a sum of products of Montgomery forms
+// back in Montgomery form).
+__device__ __forceinline__ uint64_t reduce192(uint64_t l, uint64_t m, uint32_t h, uint64_t fac, const ModCtx &mc)
+{
+    const uint64_t a = mont_redc(l, 0, mc);
+    uint64_t lo;
+    uint32_t hi = h;
+    asm("add.cc.u64 %0, %2, %3;\n\taddc.u32 %1, %1, 0;" : "=l"(lo), "+r"(hi) : "l"(m), "l"(a));
+    const uint64_t b = mont_redc(lo, hi, mc);
+    return canon(mont_mul(b, fac, mc), mc.p);
+}
+
 // ------------------------------------------------- Algorithms 2 and 3 (FP64)
 // Modular product of canonical x, y < p < 2^50 held in doubles, u = 1/(double)p.
 // h + l = x*y exactly (FMA error-free product); c is the quotient within one;

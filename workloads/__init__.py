@@ -29,6 +29,7 @@ __all__ = [
     "Workload", "is_prime", "random_prime", "make_uniform", "make_zipf",
     "config_tiny", "config_large", "config_width", "config_batched",
     "served_requests", "sort_by_group", "shuffled", "config_interp", "interp_group_sizes",
+    "random_ntt_prime",
 ]
 
 MR_BASES = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
@@ -69,6 +70,20 @@ def random_prime(bits: int, seed: int) -> int:
         c = int(rng.integers(lo, hi, dtype=np.uint64)) | 1
         if c < hi and is_prime(c):
             return c
+
+
+def random_ntt_prime(bits: int, e: int, seed: int) -> int:
+    """A prime p = k * 2^e + 1 with 2^(bits-1) <= p < 2^bits (NTTs of every order
+    up to 2^e exist in F_p), from seeded odd multipliers k."""
+    if not (e + 2 <= bits <= 63):
+        raise ValueError("need e + 2 <= bits <= 63")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo, hi = 1 << (bits - 1 - e), 1 << (bits - e)
+    while True:
+        k = int(rng.integers(lo, hi, dtype=np.uint64)) | 1
+        p = k * (1 << e) + 1
+        if p < (1 << bits) and is_prime(p):
+            return p
 
 
 @dataclasses.dataclass
@@ -206,11 +221,13 @@ def config_large(seed: int = SEED_LARGE, s: int = 1_000_000, T: int = 1024, bits
                      name=f"large n=9 s={s} G=5041 zipf1.1 T={T} p{bits}")
 
 
-def config_width(bits: int, seed: int = SEED_WIDTH, s: int = 4_000_000, T: int = 4096) -> Workload:
-    """The tiny generator at 4e6 terms and T=4096, with a 50-bit or 62-bit prime."""
-    p = random_prime(bits, seed + bits)
+def config_width(bits: int, seed: int = SEED_WIDTH, s: int = 4_000_000, T: int = 4096,
+                 ntt: bool = False) -> Workload:
+    """The tiny generator at 4e6 terms and T=4096, with a 50-bit or 62-bit prime
+    (with ntt=True a prime p = k * 2^20 + 1, as the fast method needs)."""
+    p = random_ntt_prime(bits, 20, seed + bits) if ntt else random_prime(bits, seed + bits)
     return make_uniform(n=6, s=s, p=p, deg12=8, deg_rest=5, T=T, seed=seed + 1,
-                        name=f"width n=6 s={s} G=81 T={T} p{bits}")
+                        name=f"width n=6 s={s} G=81 T={T} p{bits}{' ntt' if ntt else ''}")
 
 
 def config_batched(seed: int = SEED_BATCH, count: int = 512, s_min: int = 1_000,
