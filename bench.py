@@ -288,6 +288,82 @@ def bench_multiprime(pe, torch, w, nprimes=4, reps=5):
             "note": "create/create_like host-timed; batch and loop timed with CUDA events, inputs resident"}
 
 
+def _fast_counts(off, T):
+    """Shoup products (NTT butterflies and scalings) and Montgomery products
+    (pointwise) of the fast method's product trees and series for column
+    offsets `off` and T points, following the library's block structure."""
+    Tp = 64
+    while Tp < T:
+        Tp *= 2
+    lg = lambda x: x.bit_length() - 1
+    ntt = lambda N: (N // 2) * lg(N)
+    shoup = mont = 0
+    series_shoup = sum(3 * ntt(4 << k) + (4 << k) + 3 * ntt(2 << k) + (2 << k) for k in range(lg(Tp)))
+    series_shoup += 3 * ntt(2 * Tp) + 2 * Tp
+    series_mont = sum((4 << k) + (2 << k) for k in range(lg(Tp))) + 2 * Tp
+    for g in range(len(off) - 1):
+        n = int(off[g + 1] - off[g])
+        for a in range(0, n, Tp):
+            d = min(Tp, n - a)
+            L = 32
+            while L < d:
+                for ps in range(0, d, 2 * L):
+                    la = min(L, d - ps)
+                    if min(L, d - ps - la):
+                        shoup += 6 * ntt(2 * L) + 2 * 2 * L
+                        mont += 3 * 2 * L
+                L *= 2
+            shoup += series_shoup
+            mont += series_mont
+    return shoup, mont
+
+
+def bench_fast(pe, torch, mhz, reps=3):
+    """The fast method (Sect. 2.3.1) beside the matrix method on NTT-friendly
+    62-bit primes: the width workload (81 groups of ~49,000 terms) at T = 4096
+    and 1024, and the large workload's shape (5,041 Zipf groups) at T = 1024."""
+    rates = pe.int_pipe_rates()
+    wide, hi = rates["mad_lo"] / rates["mad_wide"], rates["mad_lo"] / rates["mad_hi"]
+    shoup_slots, mont_slots = 5 * wide + hi + 4, 8 * wide + 2 * hi + 4
+    peak = NUM_SMS * rates["mad_lo"] * mhz * 1e6
+    res = []
+    cases = [wl.config_width(62, ntt=True), wl.config_width(62, ntt=True, T=1024),
+             wl.make_zipf(n=9, s=1_000_000, p=wl.random_ntt_prime(62, 20, 5), deg12=70, deg_rest=20, T=1024,
+                          seed=wl.SEED_LARGE + 1, a=1.1, name="large shape n=9 s=1e6 G=5041 T=1024 p62 ntt")]
+    for w in cases:
+        poly = pe.Poly.from_workload(w)
+        out_m = torch.empty((w.T, poly.G), dtype=torch.int64, device="cuda")
+        out_f = torch.empty_like(out_m)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        poly.run(w.beta, w.T, out=out_m)
+        poly.run_fast(w.beta, w.T, out=out_f)
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            poly.run(w.beta, w.T, out=out_m)
+        ev[1].record()
+        for _ in range(reps):
+            poly.run_fast(w.beta, w.T, out=out_f)
+        ev[2].record()
+        torch.cuda.synchronize()
+        m_ms, f_ms = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
+        identical = bool(torch.equal(out_m, out_f))
+        _, off = poly.monomials(w.beta)
+        sh, mo = _fast_counts(off, w.T)
+        slots = sh * shoup_slots + mo * mont_slots
+        res.append({"workload": w.name, "matrix_ms": m_ms, "fast_ms": f_ms, "fast_over_matrix": m_ms / f_ms,
+                    "identical": identical, "fast_term_points_per_s": w.s * w.T / (f_ms * 1e-3),
+                    "shoup_products": sh, "montgomery_products": mo,
+                    "products_per_term_point": (sh + mo) / (w.s * w.T),
+                    "roofline": {"bound": "alu", "achieved": slots / (f_ms * 1e-3) / 1e9, "peak": peak / 1e9,
+                                 "unit": "Gslot/s", "frac": slots / (f_ms * 1e-3) / peak,
+                                 "algorithmic": f"Shoup products {shoup_slots:.1f} mad.lo slots, Montgomery "
+                                                f"{mont_slots:.1f}; counted from the block structure"}})
+        poly.close()
+        del out_m, out_f
+    return res
+
+
 def _vdm_counts(off):
     """Algorithmic multiplies of the solver: exact 64x64-bit products of the
     product tree and of the correlation, fixed-multiplier products of Horner."""
@@ -514,6 +590,7 @@ def run_ours(args):
         line["interpolation"] = bench_interp(pe, torch, mhz)
         if args.config == "large":
             line["multi_prime"] = bench_multiprime(pe, torch, w)
+            line["fast_method"] = bench_fast(pe, torch, mhz)
     poly.close()
     if world == 1 and not args.no_extras:
         del out, flush

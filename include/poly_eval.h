@@ -210,6 +210,8 @@ typedef struct {
     uint64_t spans;           /* groups whose terms cross work-item boundaries */
     uint64_t padded_terms;    /* chunks * K */
     uint64_t tail_points;     /* last points run as one-slab items after the others (0: none) */
+    uint32_t method;          /* what poly_eval_run uses for this T: 0 matrix method, 1 fast method
+                                 (poly_eval_tune measured it faster; NTT-friendly p) */
 } pe_plan_info;
 
 pe_status poly_eval_plan_info(pe_poly *poly, uint64_t T, pe_plan_info *info);

@@ -58,7 +58,7 @@ class _Tiles(ctypes.Structure):
 class _PlanInfo(ctypes.Structure):
     _fields_ = [("tiles", _Tiles), ("variant", ctypes.c_int), ("chunks", ctypes.c_uint64),
                 ("items", ctypes.c_uint64), ("spans", ctypes.c_uint64), ("padded_terms", ctypes.c_uint64),
-                ("tail_points", ctypes.c_uint64)]
+                ("tail_points", ctypes.c_uint64), ("method", ctypes.c_uint32)]
 
 
 class _Job(ctypes.Structure):
@@ -295,7 +295,8 @@ class Poly:
         return {"K": info.tiles.K, "slabs": info.tiles.slabs, "tchunk": info.tiles.tchunk,
                 "warps_per_block": info.tiles.warps_per_block, "variant": info.variant,
                 "chunks": info.chunks, "items": info.items, "spans": info.spans,
-                "padded_terms": info.padded_terms, "tail_points": info.tail_points}
+                "padded_terms": info.padded_terms, "tail_points": info.tail_points,
+                "method": "fast" if info.method == 1 else "matrix"}
 
     def launches_per_run(self, T: int) -> int:
         n = ctypes.c_uint32()

@@ -1048,6 +1048,14 @@ extern "C" pe_status poly_eval_plan_info(pe_poly *P, uint64_t T, pe_plan_info *i
     info->items = (uint64_t)P->plan.U * P->plan.Q + (t.tailT ? (uint64_t)P->tail_plan.U * P->tail_plan.Q : 0);
     info->spans = P->plan.S;
     info->padded_terms = (uint64_t)P->plan.NC * t.K;
+    {
+        const TuneEntry *te = tune_lookup(P, T);
+        info->method = P->requested_variant == PE_MODMUL_AUTO && !P->forced.K && !P->forced.slabs &&
+                               !P->forced.tchunk && !P->forced.warps_per_block && !P->forced.tail && te &&
+                               te->method == 1 && fast_applicable(P->p, T)
+                           ? 1u
+                           : 0u;
+    }
     info->tail_points = t.tailT;
     return PE_OK;
 }
@@ -1103,6 +1111,17 @@ extern "C" pe_status poly_eval_launches_per_run(pe_poly *P, uint64_t T, uint32_t
 
 extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t t0, uint64_t *out,
                                    void *stream)
+{
+    // The tuner's choice of method for this shape, unless a product or tiles were forced.
+    if (P && P->requested_variant == PE_MODMUL_AUTO && !P->forced.K && !P->forced.slabs && !P->forced.tchunk &&
+        !P->forced.warps_per_block && !P->forced.tail && fast_applicable(P->p, T)) {
+        const TuneEntry *te = tune_lookup(P, T);
+        if (te && te->method == 1) return poly_eval_run_fast(P, beta, T, t0, out, stream);
+    }
+    return run_matrix(P, beta, T, t0, out, stream);
+}
+
+pe_status pe::run_matrix(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t t0, uint64_t *out, void *stream)
 {
     if (!P) {
         set_error("NULL poly");

@@ -335,6 +335,16 @@ void fast_plan_delete(FastPlan *f) { delete f; }
 
 using namespace pe;
 
+static bool fast_applicable(uint64_t p, uint64_t T, uint32_t *logTp);
+
+namespace pe {
+bool fast_applicable(uint64_t p, uint64_t T)
+{
+    uint32_t l;
+    return ::fast_applicable(p, T, &l);
+}
+}  // namespace pe
+
 static bool fast_applicable(uint64_t p, uint64_t T, uint32_t *logTp)
 {
     uint32_t lt = 6;

@@ -89,13 +89,13 @@ extern "C" pe_status poly_eval_tune(pe_poly *P, uint64_t T, pe_tiles *best, doub
                 P->requested_variant = v;
                 P->plan.valid = false;
                 P->tail_plan.valid = false;
-                pe_status s = poly_eval_run(P, beta.data(), T, 1, out.as<uint64_t>(), st);  // warm-up + plan
+                pe_status s = run_matrix(P, beta.data(), T, 1, out.as<uint64_t>(), st);  // warm-up + plan
                 if (s != PE_OK) {
                     result = s;
                     break;
                 }
                 cudaEventRecord(a, st);
-                for (int r = 0; r < 3; ++r) poly_eval_run(P, beta.data(), T, 1, out.as<uint64_t>(), st);
+                for (int r = 0; r < 3; ++r) run_matrix(P, beta.data(), T, 1, out.as<uint64_t>(), st);
                 cudaEventRecord(b, st);
                 if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
                     result = cuda_fail(e, "tune");
@@ -131,13 +131,13 @@ extern "C" pe_status poly_eval_tune(pe_poly *P, uint64_t T, pe_tiles *best, doub
             P->requested_variant = bestE.variant;
             P->plan.valid = false;
             P->tail_plan.valid = false;
-            pe_status s = poly_eval_run(P, beta.data(), T, 1, out.as<uint64_t>(), st);
+            pe_status s = run_matrix(P, beta.data(), T, 1, out.as<uint64_t>(), st);
             if (s != PE_OK) {
                 result = s;
                 break;
             }
             cudaEventRecord(a, st);
-            for (int r = 0; r < 3; ++r) poly_eval_run(P, beta.data(), T, 1, out.as<uint64_t>(), st);
+            for (int r = 0; r < 3; ++r) run_matrix(P, beta.data(), T, 1, out.as<uint64_t>(), st);
             cudaEventRecord(b, st);
             if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
                 result = cuda_fail(e, "tune");
@@ -157,6 +157,25 @@ extern "C" pe_status poly_eval_tune(pe_poly *P, uint64_t T, pe_tiles *best, doub
     P->requested_variant = saved_req;
     P->plan.valid = false;
     P->tail_plan.valid = false;
+    // The fast method (Sect. 2.3.1) where the prime allows it.
+    if (result == PE_OK && saved_req == PE_MODMUL_AUTO && fast_applicable(P->p, T)) {
+        pe_status s = poly_eval_run_fast(P, beta.data(), T, 1, out.as<uint64_t>(), st);
+        if (s == PE_OK) {
+            cudaEventRecord(a, st);
+            for (int r = 0; r < 3; ++r) poly_eval_run_fast(P, beta.data(), T, 1, out.as<uint64_t>(), st);
+            cudaEventRecord(b, st);
+            if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
+                result = cuda_fail(e, "tune");
+            } else {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                if (ms / 3.0 < bestE.ms) {
+                    bestE.ms = ms / 3.0;
+                    bestE.method = 1;
+                }
+            }
+        }
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaStreamDestroy(st);
@@ -192,7 +211,8 @@ extern "C" pe_status poly_eval_tune_save(const char *path)
     for (const auto &kv : g_tune)
         f << "{\"key\": \"" << kv.first << "\", \"K\": " << kv.second.K << ", \"wpb\": " << kv.second.wpb
           << ", \"variant\": " << kv.second.variant << ", \"ms\": " << kv.second.ms << ", \"slabs\": "
-          << kv.second.kslabs << ", \"tchunk\": " << kv.second.Tc << ", \"tail\": " << kv.second.tail << "}\n";
+          << kv.second.kslabs << ", \"tchunk\": " << kv.second.Tc << ", \"tail\": " << kv.second.tail
+          << ", \"method\": " << kv.second.method << "}\n";
     return PE_OK;
 }
 
@@ -234,6 +254,10 @@ extern "C" pe_status poly_eval_tune_load(const char *path)
             t.Tc = tc;
             t.tail = tl;
         }
+        unsigned meth = 0;
+        const size_t mp = line.find("\"method\":");
+        if (mp != std::string::npos && sscanf(line.c_str() + mp, "\"method\": %u", &meth) == 1 && meth <= 1)
+            t.method = meth;
         g_tune[line.substr(k0 + 8, k1 - k0 - 8)] = t;
     }
     return PE_OK;

@@ -69,3 +69,21 @@ def test_requirements():
     with pytest.raises(pe.PolyEvalError):
         poly.run_fast(w.beta, 8192)                         # T above 4096
     poly.close()
+
+
+def test_tuner_picks_the_faster_method(tmp_path):
+    """On large groups at T = 4,096 the fast method wins by a wide margin; after
+    tuning, poly_eval_run dispatches to it and still matches the matrix method."""
+    w = wl.make_uniform(n=6, s=200_000, p=P_NTT50, deg12=2, deg_rest=7, T=4096, seed=19)
+    poly = pe.Poly.from_workload(w)
+    plain = pe.to_u64(poly.run(w.beta, w.T))
+    pe.tune(poly, w.T)
+    assert poly.plan_info(w.T)["method"] == "fast"
+    assert np.array_equal(pe.to_u64(poly.run(w.beta, w.T)), plain)
+    path = str(tmp_path / "tune.jsonl")
+    pe.tune_save(path)
+    assert '"method": 1' in open(path).read()
+    poly.set_tiles(K=8)                                    # forced tiles: the matrix method again
+    assert poly.plan_info(w.T)["method"] == "matrix"
+    assert np.array_equal(pe.to_u64(poly.run(w.beta, w.T)), plain)
+    poly.close()
