@@ -298,9 +298,11 @@ def _fast_counts(off, T):
     lg = lambda x: x.bit_length() - 1
     ntt = lambda N: (N // 2) * lg(N)
     shoup = mont = 0
-    series_shoup = sum(3 * ntt(4 << k) + (4 << k) + 3 * ntt(2 << k) + (2 << k) for k in range(lg(Tp)))
+    # Newton step k: five NTTs of size 2k (one transform of h serves both products), two scalings, two
+    # pointwise products; then N h with three NTTs of size 2Tp.
+    series_shoup = sum(5 * ntt(2 << k) + 2 * (2 << k) for k in range(lg(Tp)))
     series_shoup += 3 * ntt(2 * Tp) + 2 * Tp
-    series_mont = sum((4 << k) + (2 << k) for k in range(lg(Tp))) + 2 * Tp
+    series_mont = sum(2 * (2 << k) for k in range(lg(Tp))) + 2 * Tp
     for g in range(len(off) - 1):
         n = int(off[g + 1] - off[g])
         for a in range(0, n, Tp):
@@ -324,7 +326,7 @@ def bench_fast(pe, torch, mhz, reps=3):
     and 1024, and the large workload's shape (5,041 Zipf groups) at T = 1024."""
     rates = pe.int_pipe_rates()
     wide, hi = rates["mad_lo"] / rates["mad_wide"], rates["mad_lo"] / rates["mad_hi"]
-    shoup_slots, mont_slots = 5 * wide + hi + 4, 8 * wide + 2 * hi + 4
+    shoup_slots, mont_slots = 3 * wide + 2 * hi + 4, 8 * wide + 2 * hi + 4   # lazy Shoup product; Montgomery
     peak = NUM_SMS * rates["mad_lo"] * mhz * 1e6
     res = []
     cases = [wl.config_width(62, ntt=True), wl.config_width(62, ntt=True, T=1024),

@@ -51,55 +51,111 @@ struct FastBlockT {
 
 __device__ __forceinline__ uint64_t lazy2(uint64_t x, uint64_t p2) { return x >= p2 ? x - p2 : x; }
 
-// Forward NTT (decimation in frequency, natural order in, bit-reversed out) of
-// NA arrays of size N = 2^logN in shared memory, values in [0, 2p).
-template <int NA>
-__device__ void ntt_fwd(uint64_t *const *arr, uint32_t logN, const FastTab &tb, uint64_t p, uint64_t p2)
+// Shoup's product x*w mod p for a twiddle w (wq = floor(w 2^64 / p)), in [0, 2p).
+__device__ __forceinline__ uint64_t twmul(uint64_t x, uint64_t w, uint64_t wq, const ModCtx &mc)
 {
-    const uint32_t half = 1u << (logN - 1);
-    for (int logh = (int)logN - 1; logh >= 0; --logh) {
-        const uint32_t h = 1u << logh;
-        const uint32_t sh = tb.lognmax - (uint32_t)(logh + 1);
-        for (uint32_t b = threadIdx.x; b < half; b += blockDim.x) {
-            const uint32_t j = b & (h - 1), s = (b - j) << 1;
+    return lazy2(barrett_mul_lazy4_mad(x, w, wq, 0 - mc.p), mc.p2);
+}
+
+// Forward NTT (decimation in frequency, natural order in, bit-reversed out) of
+// NA arrays of size N = 2^logN in shared memory, values in [0, 2p).  Two
+// stages per pass (radix 4: the stage of half-size h, then h/2, on the four
+// points s+j, s+j+h/2, s+j+h, s+j+3h/2), after one radix-2 stage if logN is odd.
+template <int NA>
+__device__ void ntt_fwd(uint64_t *const *arr, uint32_t logN, const FastTab &tb, const ModCtx &mc)
+{
+    const uint64_t p2 = mc.p2;
+    const uint32_t N = 1u << logN;
+    int logh = (int)logN - 1;
+    if (logN & 1) {
+        const uint32_t h = 1u << logh, sh = tb.lognmax - (uint32_t)(logh + 1);
+        for (uint32_t j = threadIdx.x; j < h; j += blockDim.x) {
             const uint64_t w = tb.W[j << sh], wq = tb.Wq[j << sh];
 #pragma unroll
             for (int k = 0; k < NA; ++k) {
                 uint64_t *a = arr[k];
-                const uint64_t u = a[s + j], v = a[s + j + h];
-                a[s + j] = lazy2(u + v, p2);
-                a[s + j + h] = barrett_mul(u - v + p2, w, wq, p);
+                const uint64_t u = a[j], v = a[j + h];
+                a[j] = lazy2(u + v, p2);
+                a[j + h] = twmul(u - v + p2, w, wq, mc);
+            }
+        }
+        __syncthreads();
+        --logh;
+    }
+    for (; logh >= 1; logh -= 2) {
+        const uint32_t h = 1u << logh, q = h >> 1;
+        const uint32_t sh1 = tb.lognmax - (uint32_t)(logh + 1), sh2 = tb.lognmax - (uint32_t)logh;
+        for (uint32_t b = threadIdx.x; b < N / 4; b += blockDim.x) {
+            const uint32_t j = b & (q - 1), s = (b - j) << 2;
+            const uint64_t w1 = tb.W[j << sh1], w1q = tb.Wq[j << sh1];
+            const uint64_t w3 = tb.W[(j + q) << sh1], w3q = tb.Wq[(j + q) << sh1];
+            const uint64_t w2 = tb.W[j << sh2], w2q = tb.Wq[j << sh2];
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                uint64_t *a = arr[k] + s + j;
+                const uint64_t a0 = a[0], a1 = a[q], a2 = a[2 * q], a3 = a[3 * q];
+                const uint64_t b0 = lazy2(a0 + a2, p2), b2 = twmul(a0 - a2 + p2, w1, w1q, mc);
+                const uint64_t b1 = lazy2(a1 + a3, p2), b3 = twmul(a1 - a3 + p2, w3, w3q, mc);
+                a[0] = lazy2(b0 + b1, p2);
+                a[q] = twmul(b0 - b1 + p2, w2, w2q, mc);
+                a[2 * q] = lazy2(b2 + b3, p2);
+                a[3 * q] = twmul(b2 - b3 + p2, w2, w2q, mc);
             }
         }
         __syncthreads();
     }
 }
 
-// Inverse NTT (decimation in time, bit-reversed in, natural out), scaled by N^-1.
+// Inverse NTT (decimation in time, bit-reversed in, natural out), scaled by
+// N^-1; radix 4 as above (stages of half-size q, then 2q), after one radix-2
+// stage of half-size 1 (twiddle 1) if logN is odd.
 template <int NA>
-__device__ void ntt_inv(uint64_t *const *arr, uint32_t logN, const FastTab &tb, uint64_t p, uint64_t p2)
+__device__ void ntt_inv(uint64_t *const *arr, uint32_t logN, const FastTab &tb, const ModCtx &mc)
 {
-    const uint32_t half = 1u << (logN - 1);
-    for (uint32_t logh = 0; logh < logN; ++logh) {
-        const uint32_t h = 1u << logh;
-        const uint32_t sh = tb.lognmax - (logh + 1);
-        for (uint32_t b = threadIdx.x; b < half; b += blockDim.x) {
-            const uint32_t j = b & (h - 1), s = (b - j) << 1;
-            const uint64_t w = tb.Wi[j << sh], wq = tb.Wiq[j << sh];
+    const uint64_t p2 = mc.p2;
+    const uint32_t N = 1u << logN;
+    uint32_t logh = 0;
+    if (logN & 1) {
+        for (uint32_t b = threadIdx.x; b < N / 2; b += blockDim.x) {
 #pragma unroll
             for (int k = 0; k < NA; ++k) {
-                uint64_t *a = arr[k];
-                const uint64_t u = a[s + j], v = barrett_mul(a[s + j + h], w, wq, p);
-                a[s + j] = lazy2(u + v, p2);
-                a[s + j + h] = lazy2(u - v + p2, p2);
+                uint64_t *a = arr[k] + 2 * b;
+                const uint64_t u = a[0], v = a[1];
+                a[0] = lazy2(u + v, p2);
+                a[1] = lazy2(u - v + p2, p2);
+            }
+        }
+        __syncthreads();
+        logh = 1;
+    }
+    for (; logh < logN; logh += 2) {
+        const uint32_t q = 1u << logh;
+        const uint32_t shq = tb.lognmax - (logh + 1), shh = tb.lognmax - (logh + 2);
+        for (uint32_t b = threadIdx.x; b < N / 4; b += blockDim.x) {
+            const uint32_t j = b & (q - 1), s = (b - j) << 2;
+            const uint64_t wa = tb.Wi[j << shq], waq = tb.Wiq[j << shq];
+            const uint64_t wb = tb.Wi[j << shh], wbq = tb.Wiq[j << shh];
+            const uint64_t wc = tb.Wi[(j + q) << shh], wcq = tb.Wiq[(j + q) << shh];
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                uint64_t *a = arr[k] + s + j;
+                const uint64_t a0 = a[0], a2 = a[2 * q];
+                const uint64_t v1 = twmul(a[q], wa, waq, mc), v3 = twmul(a[3 * q], wa, waq, mc);
+                const uint64_t b0 = lazy2(a0 + v1, p2), b1 = lazy2(a0 - v1 + p2, p2);
+                const uint64_t b2 = lazy2(a2 + v3, p2), b3 = lazy2(a2 - v3 + p2, p2);
+                const uint64_t v2 = twmul(b2, wb, wbq, mc), v4 = twmul(b3, wc, wcq, mc);
+                a[0] = lazy2(b0 + v2, p2);
+                a[2 * q] = lazy2(b0 - v2 + p2, p2);
+                a[q] = lazy2(b1 + v4, p2);
+                a[3 * q] = lazy2(b1 - v4 + p2, p2);
             }
         }
         __syncthreads();
     }
     const uint64_t ni = tb.ninv[2 * logN], niq = tb.ninv[2 * logN + 1];
-    for (uint32_t i = threadIdx.x; i < 2 * half; i += blockDim.x)
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
 #pragma unroll
-        for (int k = 0; k < NA; ++k) arr[k][i] = barrett_mul(arr[k][i], ni, niq, p);
+        for (int k = 0; k < NA; ++k) arr[k][i] = twmul(arr[k][i], ni, niq, mc);
     __syncthreads();
 }
 
@@ -199,7 +255,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_merge(const FastPairT *__
     __syncthreads();
     {
         uint64_t *const arr[4] = {X, Y, C, E};
-        ntt_fwd<4>(arr, logL + 1, tb, p, p2);
+        ntt_fwd<4>(arr, logL + 1, tb, mc);
     }
     for (uint32_t i = threadIdx.x; i < N2; i += blockDim.x) {
         const uint64_t x = X[i], y = Y[i];
@@ -209,7 +265,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_merge(const FastPairT *__
     __syncthreads();
     {
         uint64_t *const arr[2] = {X, C};
-        ntt_inv<2>(arr, logL + 1, tb, p, p2);
+        ntt_inv<2>(arr, logL + 1, tb, mc);
     }
     const uint32_t d = pr.la + pr.lb;
     for (uint32_t k = threadIdx.x; k < d; k += blockDim.x) {
@@ -240,36 +296,37 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_series(const FastBlockT *
     __syncthreads();
     for (uint32_t logk = 0; logk < logTp; ++logk) {
         const uint32_t k = 1u << logk;
-        // e = (D mod z^2k) * h, size 4k
-        for (uint32_t i = threadIdx.x; i < 4 * k; i += blockDim.x) {
-            X[i] = i == 0 ? mc.r1 : (i < 2 * k && i <= bk.d ? D[i - 1] : 0);
+        // e = (D mod z^2k) * h with a cyclic product of size 2k: the product has
+        // degree < 3k, so only its coefficients [0, k) wrap and e_[k,2k) is exact.
+        for (uint32_t i = threadIdx.x; i < 2 * k; i += blockDim.x) {
+            X[i] = i == 0 ? mc.r1 : (i <= bk.d ? D[i - 1] : 0);
             Y[i] = i < k ? h[i] : 0;
         }
         __syncthreads();
         {
             uint64_t *const arr[2] = {X, Y};
-            ntt_fwd<2>(arr, logk + 2, tb, p, p2);
-        }
-        for (uint32_t i = threadIdx.x; i < 4 * k; i += blockDim.x) X[i] = mont_mul(X[i], Y[i], mc);
-        __syncthreads();
-        {
-            uint64_t *const arr[1] = {X};
-            ntt_inv<1>(arr, logk + 2, tb, p, p2);
-        }
-        // g = h * e_[k, 2k) mod z^k, size 2k
-        for (uint32_t i = threadIdx.x; i < 2 * k; i += blockDim.x) Y[i] = i < k ? X[k + i] : 0;
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < 2 * k; i += blockDim.x) X[i] = i < k ? h[i] : 0;
-        __syncthreads();
-        {
-            uint64_t *const arr[2] = {X, Y};
-            ntt_fwd<2>(arr, logk + 1, tb, p, p2);
+            ntt_fwd<2>(arr, logk + 1, tb, mc);
         }
         for (uint32_t i = threadIdx.x; i < 2 * k; i += blockDim.x) X[i] = mont_mul(X[i], Y[i], mc);
         __syncthreads();
         {
             uint64_t *const arr[1] = {X};
-            ntt_inv<1>(arr, logk + 1, tb, p, p2);
+            ntt_inv<1>(arr, logk + 1, tb, mc);
+        }
+        // g = h * e_[k,2k) mod z^k, reusing the transform of h (still in Y).
+        for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) X[i] = X[k + i];
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) X[k + i] = 0;
+        __syncthreads();
+        {
+            uint64_t *const arr[1] = {X};
+            ntt_fwd<1>(arr, logk + 1, tb, mc);
+        }
+        for (uint32_t i = threadIdx.x; i < 2 * k; i += blockDim.x) X[i] = mont_mul(X[i], Y[i], mc);
+        __syncthreads();
+        {
+            uint64_t *const arr[1] = {X};
+            ntt_inv<1>(arr, logk + 1, tb, mc);
         }
         for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) h[k + i] = X[i] ? p2 - X[i] : 0;
         __syncthreads();
@@ -282,13 +339,13 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_series(const FastBlockT *
     __syncthreads();
     {
         uint64_t *const arr[2] = {X, Y};
-        ntt_fwd<2>(arr, logTp + 1, tb, p, p2);
+        ntt_fwd<2>(arr, logTp + 1, tb, mc);
     }
     for (uint32_t i = threadIdx.x; i < 2 * Tp; i += blockDim.x) X[i] = mont_mul(X[i], Y[i], mc);
     __syncthreads();
     {
         uint64_t *const arr[1] = {X};
-        ntt_inv<1>(arr, logTp + 1, tb, p, p2);
+        ntt_inv<1>(arr, logTp + 1, tb, mc);
     }
     for (uint32_t r = threadIdx.x; r < T; r += blockDim.x) series[(uint64_t)blockIdx.x * T + r] = X[r];
 }
