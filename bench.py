@@ -66,8 +66,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large",
-                    choices=["large", "large30", "tiny", "width62", "width50", "batched", "served"])
+                    choices=["large", "large30", "tiny", "width62", "width62ntt", "width50", "batched", "served"])
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--method", default="auto", choices=["auto", "matrix", "fast"],
+                    help="auto: what poly_eval_run picks (the tuner's choice); fast: poly_eval_run_fast")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-burst", type=int, default=1500)
@@ -89,6 +91,8 @@ def make_workload(name):
         return wl.config_tiny()
     if name == "width62":
         return wl.config_width(62)
+    if name == "width62ntt":
+        return wl.config_width(62, ntt=True)
     return wl.config_width(50)
 
 
@@ -320,6 +324,20 @@ def _fast_counts(off, T):
     return shoup, mont
 
 
+def _fast_launches(off, T):
+    """Kernel launches of one fast-method run: power tables, Step A, leaves, the
+    merge levels some block reaches, series, sum."""
+    Tp = 64
+    while Tp < T:
+        Tp *= 2
+    dmax = max(min(Tp, int(off[g + 1] - off[g])) for g in range(len(off) - 1))
+    levels, L = 0, 32
+    while L < dmax:
+        levels += 1
+        L *= 2
+    return 5 + levels
+
+
 def bench_fast(pe, torch, mhz, reps=3):
     """The fast method (Sect. 2.3.1) beside the matrix method on NTT-friendly
     62-bit primes: the width workload (81 groups of ~49,000 terms) at T = 4096
@@ -483,6 +501,8 @@ def run_ours(args):
     variant = args.variant
     if variant == "auto" and args.config == "width50":
         variant = "fp64"
+    if variant == "auto" and args.method == "matrix":    # an explicit product keeps poly_eval_run on the matrix method
+        variant = "barrett32" if int(w.p) < (1 << 30) else "barrett64"
     from paper_2004_11571_gb300 import sharding
     t0, _ = sharding.weak_block(int(w.T), w.t0, rank)   # each rank: its own block of T points
     poly = pe.Poly.from_workload(w, variant=variant)
@@ -494,8 +514,9 @@ def run_ours(args):
     out = torch.empty((T, G), dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    run = poly.run_fast if args.method == "fast" else poly.run
     for _ in range(max(args.warmup, 0)):
-        poly.run(w.beta, T, t0, out=out, stream=stream)
+        run(w.beta, T, t0, out=out, stream=stream)
         flush.zero_()
     barrier()
     clocks = ClockSampler(local)
@@ -507,7 +528,7 @@ def run_ours(args):
     for a, b in evs:
         flush.zero_()
         a.record(stream)
-        poly.run(w.beta, T, t0, out=out, stream=stream)
+        run(w.beta, T, t0, out=out, stream=stream)
         b.record(stream)
     barrier()
     clk = clocks.stop()
@@ -522,6 +543,10 @@ def run_ours(args):
     value = s * T * world * args.steps / (max_total_ms * 1e-3)
     plan = poly.plan_info(T)
     launches = poly.launches_per_run(T) * args.steps
+    fast_off = None
+    if args.method == "fast" or (args.method == "auto" and plan["method"] == "fast"):
+        _, fast_off = poly.monomials(w.beta)
+        launches = _fast_launches(fast_off, T) * args.steps
 
     # End to end through the C ABI with host buffers.
     host_out = torch.empty((T, G), dtype=torch.int64, pin_memory=True).numpy()
@@ -531,7 +556,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t_start = time.perf_counter()
         p2 = pe.Poly(w.p, w.coeffs, w.exps, variant=variant, sorted_hint=True)
-        p2.run(w.beta, T, t0, out=host_out)
+        (p2.run_fast if args.method == "fast" else p2.run)(w.beta, T, t0, out=host_out)
         p2.close()
         e2e_t.append(time.perf_counter() - t_start)
     e2e_val = s * T / statistics.median(e2e_t)
@@ -545,7 +570,20 @@ def run_ours(args):
     tps_b = s * T / (t_b / runs * 1e-3) if runs and t_b > 0 else None
     mhz = clk["sm_mhz"] or 1920.0
     roof = None
-    if variant != "fp64" and tps_b:
+    if fast_off is not None:
+        rates = pe.int_pipe_rates()
+        wide, hi = rates["mad_lo"] / rates["mad_wide"], rates["mad_lo"] / rates["mad_hi"]
+        sh, mo = _fast_counts(fast_off, T)
+        slots = sh * (3 * wide + 2 * hi + 4) + mo * (8 * wide + 2 * hi + 4)
+        step_s = statistics.mean(step_ms) * 1e-3
+        peak = NUM_SMS * rates["mad_lo"] * mhz * 1e6 / 1e9
+        roof = {"bound": "alu", "achieved": slots / step_s / 1e9, "peak": peak, "unit": "Gslot/s",
+                "frac": slots / step_s / 1e9 / peak, "traffic": None, "kernel": "fast method (all kernels)",
+                "algorithmic": f"{sh} Shoup and {mo} Montgomery products per run (NTT butterflies, scalings, "
+                               f"pointwise products), counted from the block structure",
+                "peak_source": f"{NUM_SMS} SMs x {rates['mad_lo']:.1f} mad.lo.u32 per SM-clock (measured) x "
+                               f"{mhz:.0f} MHz (median sampled SM clock)"}
+    elif variant != "fp64" and tps_b:
         rates = pe.int_pipe_rates()
         cost = {"lo": 1.0, "hi": rates["mad_lo"] / rates["mad_hi"], "wide": rates["mad_lo"] / rates["mad_wide"]}
         slots = sum(n * cost[k] for k, n in OPS_PER_TP[vkey].items())
