@@ -55,6 +55,8 @@ struct VdmTile {
     uint64_t pbase;   // partial of chunk kappa, output j: part[pbase + kappa * n + j]
 };
 
+__device__ __forceinline__ uint64_t lazy2v(uint64_t x, uint64_t p2) { return x >= p2 ? x - p2 : x; }
+
 // x in [0, 3p) to [0, p).
 __device__ __forceinline__ uint64_t canon3(uint64_t x, const ModCtx &mc)
 {
@@ -258,6 +260,73 @@ __global__ void __launch_bounds__(kVdmTile) k_vdm_finish(const VdmTile *__restri
     vdm_finish(canon3(s, mc), canon3(d, mc), zi, zR, t0_exp, t0_pos, t.g, c + t.off + i, flags, mc);
 }
 
+// A whole column of at most 128 terms in one block (no partials, one launch
+// for all such columns): P by multiplying in one factor z - z_k per step (one
+// coefficient per thread, Montgomery form, Shoup product by the plain z_k),
+// then R and P' (thread l), then Horner and c_i (thread i).
+constexpr uint32_t kVdmSmall = 128;
+
+__global__ void __launch_bounds__(kVdmSmall) k_vdm_small(const VdmTile *__restrict__ tiles,
+                                                        const uint64_t *__restrict__ z,
+                                                        const uint64_t *__restrict__ img, uint64_t lda,
+                                                        uint64_t t0_exp, bool t0_pos, uint64_t *__restrict__ c,
+                                                        uint32_t *__restrict__ flags, ModCtx mc)
+{
+    __shared__ uint64_t Zs[kVdmSmall], Pa[kVdmSmall + 1], A[kVdmSmall], R[kVdmSmall], Dd[kVdmSmall];
+    const VdmTile t = tiles[blockIdx.x];
+    const uint32_t n = t.n, i = threadIdx.x;
+    const uint64_t p = mc.p, p2 = mc.p2, np = 0 - mc.p;
+    uint64_t zi = 0;
+    if (i < n) {
+        zi = z[t.off + i];
+        if (zi >= p) {
+            atomicOr(flags, 1u);
+            zi = 0;
+        }
+        Zs[i] = zi;
+        A[i] = img[(uint64_t)i * lda + t.g];
+    }
+    if (i == 0) Pa[0] = mc.r1;   // P = 1
+    __syncthreads();
+    for (uint32_t k = 0; k < n; ++k) {   // P <- P (z - z_k): degree k -> k+1, leading coefficient stays 1
+        const uint64_t zk = Zs[k];
+        const uint64_t wq = barrett_quotient_from_mont(canon(mont_mul(zk, mc.r2, mc), p), mc);
+        uint64_t nv = 0;
+        if (i <= k) {
+            const uint64_t below = i ? Pa[i - 1] : 0;
+            const uint64_t prod = lazy2v(barrett_mul_lazy4_mad(Pa[i], zk, wq, np), p2);
+            nv = lazy2v(below + p2 - prod, p2);
+        }
+        __syncthreads();
+        if (i <= k) Pa[i] = nv;
+        if (i == 0) Pa[k + 1] = mc.r1;
+        __syncthreads();
+    }
+    if (i < n) {   // R_l = sum_{k <= n-1-l} a_k P_{k+1+l}, P'_l = (l+1) P_{l+1}, plain residues
+        uint64_t lo = 0, mid = 0;
+        uint32_t h = 0;
+        for (uint32_t k = 0; k + i < n; ++k) mac192(lo, mid, h, A[k], Pa[k + 1 + i]);
+        R[i] = reduce192(lo, mid, h, mc.r2, mc);
+        lo = mid = 0;
+        h = 0;
+        mac192(lo, mid, h, (uint64_t)i + 1, Pa[i + 1]);
+        Dd[i] = reduce192(lo, mid, h, mc.r2, mc);
+    }
+    __syncthreads();
+    if (i < n) {
+        const uint64_t zR = canon(mont_mul(zi, mc.r2, mc), p);
+        const uint64_t wq = barrett_quotient_from_mont(zR, mc);
+        uint64_t sv = 0, dv = 0;
+        for (uint32_t l = n; l-- > 0;) {
+            sv = barrett_mul_lazy4_mad(sv, zi, wq, np);
+            dv = barrett_mul_lazy4_mad(dv, zi, wq, np);
+            sv = lazy2v(sv, p2) + R[l];
+            dv = lazy2v(dv, p2) + Dd[l];
+        }
+        vdm_finish(canon3(sv, mc), canon3(dv, mc), zi, zR, t0_exp, t0_pos, t.g, c + t.off + i, flags, mc);
+    }
+}
+
 // Canonical values from Montgomery form.
 __global__ void k_from_mont(const uint64_t *__restrict__ xR, uint64_t s, ModCtx mc, uint64_t *__restrict__ x)
 {
@@ -343,9 +412,19 @@ extern "C" pe_status poly_eval_vandermonde_solve(uint64_t p, uint64_t G, const u
     const uint64_t r3 = (uint64_t)(((unsigned __int128)mc.r2 * mc.r1) % p);
     // Per column: chunk length (at least 512, at most 64 chunks) and the base
     // of its partials (chunks x terms words).  Larger columns first.
-    std::vector<uint64_t> order;
-    for (uint64_t g = 0; g < G; ++g)
-        if (off[g + 1] > off[g]) order.push_back(g);
+    // Columns of at most 128 terms go to the one-launch kernel; the rest
+    // through the tree, correlation and Horner kernels.
+    std::vector<uint64_t> order, small;
+    uint64_t nlarge = 0;
+    for (uint64_t g = 0; g < G; ++g) {
+        const uint64_t n = off[g + 1] - off[g];
+        if (n > kVdmSmall) {
+            order.push_back(g);
+            nlarge = std::max(nlarge, n);
+        } else if (n) {
+            small.push_back(g);
+        }
+    }
     std::stable_sort(order.begin(), order.end(),
                      [&](uint64_t a, uint64_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
     std::vector<uint32_t> clen(G, kVdmChunk);
@@ -372,7 +451,7 @@ extern "C" pe_status poly_eval_vandermonde_solve(uint64_t p, uint64_t G, const u
     end(r_init);
     std::vector<VdmRange> r_merge, r_msum;   // level L of the tree: coefficients with more than L terms
     std::vector<uint32_t> level_L;
-    for (uint64_t L = 1; L < nmax; L *= 2) {
+    for (uint64_t L = 1; L < nlarge; L *= 2) {
         level_L.push_back((uint32_t)L);
         VdmRange m = begin();
         for (uint64_t g : order)
@@ -399,6 +478,9 @@ extern "C" pe_status poly_eval_vandermonde_solve(uint64_t p, uint64_t G, const u
     for (uint64_t g : order)
         if (chunks(g, off[g + 1] - off[g]) > 1) column(g, chunks(g, off[g + 1] - off[g]), false);
     end(r_finish);
+    VdmRange r_small = begin();
+    for (uint64_t g : small) tiles.push_back({(uint32_t)off[g], (uint32_t)(off[g + 1] - off[g]), 0, (uint32_t)g, 0, 1, 0, 0, 0});
+    end(r_small);
     if (tiles.size() > 0x7fffffffull) {
         set_error("too many columns");
         return PE_ERR_ARG;
@@ -407,17 +489,22 @@ extern "C" pe_status poly_eval_vandermonde_solve(uint64_t p, uint64_t G, const u
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     DevBuf dtiles, b0, b1, ag, dD, part, flags;
-    if ((e = dtiles.ensure(tiles.size() * sizeof(VdmTile))) != cudaSuccess ||
-        (e = b0.ensure(s * 8)) != cudaSuccess || (e = b1.ensure(s * 8)) != cudaSuccess ||
-        (e = ag.ensure(s * 8)) != cudaSuccess || (e = dD.ensure(s * 8)) != cudaSuccess ||
-        (e = part.ensure(std::max<uint64_t>(1, 2 * part_words) * 8)) != cudaSuccess ||
-        (e = flags.ensure(8)) != cudaSuccess)
+    const uint64_t sl = order.empty() ? 1 : s;   // the general path's scratch
+    if ((e = dtiles.ensure_async(tiles.size() * sizeof(VdmTile), st)) != cudaSuccess ||
+        (e = b0.ensure_async(sl * 8, st)) != cudaSuccess || (e = b1.ensure_async(sl * 8, st)) != cudaSuccess ||
+        (e = ag.ensure_async(sl * 8, st)) != cudaSuccess || (e = dD.ensure_async(sl * 8, st)) != cudaSuccess ||
+        (e = part.ensure_async(std::max<uint64_t>(1, 2 * part_words) * 8, st)) != cudaSuccess ||
+        (e = flags.ensure_async(8, st)) != cudaSuccess) {
+        cudaStreamSynchronize(st);
         return cuda_fail(e, "interpolation scratch");
+    }
     const uint32_t fl_init[2] = {0, 0xffffffffu};
     if ((e = cudaMemcpyAsync(dtiles.p, tiles.data(), tiles.size() * sizeof(VdmTile), cudaMemcpyHostToDevice, st)) !=
             cudaSuccess ||
-        (e = cudaMemcpyAsync(flags.p, fl_init, 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        (e = cudaMemcpyAsync(flags.p, fl_init, 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+        cudaStreamSynchronize(st);
         return cuda_fail(e, "interpolation upload");
+    }
     const VdmTile *T = dtiles.as<VdmTile>();
     uint64_t *bufs[2] = {b0.as<uint64_t>(), b1.as<uint64_t>()};
     uint64_t *part_s = part.as<uint64_t>(), *part_d = part_s + part_words;
@@ -429,8 +516,10 @@ extern "C" pe_status poly_eval_vandermonde_solve(uint64_t p, uint64_t G, const u
         if (tm.on) cudaEventRecord(tm.ev[k], st);
     };
     auto grid = [](const VdmRange &r) { return (unsigned)r.count; };
+    const bool general = !order.empty();
     mark(0);
-    k_vdm_init<<<grid(r_init), kVdmTile, 0, st>>>(T + r_init.at, z, images, lda, p, bufs[0], ag.as<uint64_t>(),
+    if (general)
+        k_vdm_init<<<grid(r_init), kVdmTile, 0, st>>>(T + r_init.at, z, images, lda, p, bufs[0], ag.as<uint64_t>(),
                                                   flags.as<uint32_t>());
     mark(1);
     for (size_t lv = 0; lv < r_merge.size(); ++lv) {
@@ -441,20 +530,26 @@ extern "C" pe_status poly_eval_vandermonde_solve(uint64_t p, uint64_t G, const u
             k_vdm_sum<<<grid(r_msum[lv]), kVdmTile, 0, st>>>(T + r_msum[lv].at, part_s, dst, dst, 0, mc);
     }
     mark(2);
-    k_vdm_corr<<<grid(r_corr), kVdmTile, 0, st>>>(T + r_corr.at, bufs[0], bufs[1], ag.as<uint64_t>(), bufs[0],
+    if (general)
+        k_vdm_corr<<<grid(r_corr), kVdmTile, 0, st>>>(T + r_corr.at, bufs[0], bufs[1], ag.as<uint64_t>(), bufs[0],
                                                   bufs[1], dD.as<uint64_t>(), part_s, r3, mc);
     if (r_csum.count)
         k_vdm_sum<<<grid(r_csum), kVdmTile, 0, st>>>(T + r_csum.at, part_s, bufs[0], bufs[1], 1, mc);
     mark(3);
     const uint64_t t0_exp = (p - 1 - t0 % (p - 1)) % (p - 1);
-    k_vdm_horner<<<grid(r_horner), kVdmTile, 0, st>>>(T + r_horner.at, z, bufs[0], bufs[1], dD.as<uint64_t>(),
+    if (r_small.count)
+        k_vdm_small<<<grid(r_small), kVdmSmall, 0, st>>>(T + r_small.at, z, images, lda, t0_exp, t0 > 0, c,
+                                                        flags.as<uint32_t>(), mc);
+    if (general)
+        k_vdm_horner<<<grid(r_horner), kVdmTile, 0, st>>>(T + r_horner.at, z, bufs[0], bufs[1], dD.as<uint64_t>(),
                                                       part_s, part_d, t0_exp, t0 > 0, c, flags.as<uint32_t>(), mc);
     if (r_finish.count)
         k_vdm_finish<<<grid(r_finish), kVdmTile, 0, st>>>(T + r_finish.at, z, part_s, part_d, t0_exp, t0 > 0, c,
                                                           flags.as<uint32_t>(), mc);
     mark(4);
     uint32_t fl[2] = {0, 0};
-    if ((e = cudaGetLastError()) != cudaSuccess ||
+    if ((e = cudaGetLastError()) != cudaSuccess) cudaStreamSynchronize(st);
+    if (e != cudaSuccess ||
         (e = cudaMemcpyAsync(fl, flags.p, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "interpolation");
