@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--config", default="large",
                     choices=["large", "large30", "tiny", "width62", "width62ntt", "width50", "batched", "served"])
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--tiles", default="",
+                    help="force Step B tiles K,slabs,tchunk,warps_per_block,tail (no tuning), e.g. 16,1,224,4,128")
     ap.add_argument("--method", default="auto", choices=["auto", "matrix", "fast"],
                     help="auto: what poly_eval_run picks (the tuner's choice); fast: poly_eval_run_fast")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
@@ -508,7 +510,10 @@ def run_ours(args):
     poly = pe.Poly.from_workload(w, variant=variant)
     G, T, s = poly.G, int(w.T), w.s
     tuned = None
-    if not args.no_tune and variant in ("auto",):
+    if args.tiles:
+        K, slabs, tchunk, wpb, tail = (int(x) for x in args.tiles.split(","))
+        poly.set_tiles(K=K, slabs=slabs, tchunk=tchunk, warps_per_block=wpb, tail=tail)
+    elif not args.no_tune and variant in ("auto",):
         tiles, tuned_ms = pe.tune(poly, T)          # measures tile shapes and products for this shape
         tuned = {"tiles": tiles, "ms": tuned_ms}
     out = torch.empty((T, G), dtype=torch.int64, device="cuda")

@@ -190,7 +190,7 @@ const char *poly_eval_last_error(void);
  * points.  Zero fields mean "choose automatically".
  */
 typedef struct {
-    uint32_t K;               /* terms per lane: 1, 2, 4, 8 or 16 */
+    uint32_t K;               /* terms per lane: 1, 2, 4, 8, 12 or 16 */
     uint32_t slabs;           /* slabs per work item */
     uint32_t tchunk;          /* points per work item */
     uint32_t warps_per_block; /* 1..8 (the plain Step B kernel uses at most 4) */

@@ -289,14 +289,14 @@ Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
     } else if (te) {
         t.K = te->K;
     } else {
-        // Padded slots plus the per-chunk walk: a chunk costs K products+sums
-        // and one walk entry per point.  A walk entry costs ~0.7 of a 64-bit
-        // product+sum and ~2.4 of a 32-bit one, so 32-bit products also try K=16.
+        // Padded slots plus the per-chunk cost: a chunk costs K products+sums
+        // and, per point, its partial's store and walk entry, about 1.2 of a
+        // 64-bit product+sum and 2.4 of a 32-bit one (measured on GB300: K=16
+        // with 168 registers and 12 warps per SM beats K=8 with 20 warps).
         const bool narrow = P->variant == PE_MODMUL_BARRETT32;
-        const double walk = narrow ? 2.4 : 0.7;
+        const double walk = narrow ? 2.4 : 1.2;
         double best = 1e300;
-        for (uint32_t K : {1u, 2u, 4u, 8u, 16u}) {
-            if (K == 16 && !narrow) break;
+        for (uint32_t K : {1u, 2u, 4u, 8u, 12u, 16u}) {
             const double nc = (double)count_chunks(P, K);
             const double c = nc * (K + walk);
             if (c < best * 0.98) {
@@ -993,8 +993,8 @@ extern "C" pe_status poly_eval_set_tiles(pe_poly *P, const pe_tiles *t)
     }
     pe_tiles z{};
     if (!t) t = &z;
-    if (t->K && t->K != 1 && t->K != 2 && t->K != 4 && t->K != 8 && t->K != 16) {
-        set_error("K must be 1, 2, 4, 8 or 16");
+    if (t->K && t->K != 1 && t->K != 2 && t->K != 4 && t->K != 8 && t->K != 12 && t->K != 16) {
+        set_error("K must be 1, 2, 4, 8, 12 or 16");
         return PE_ERR_ARG;
     }
     if (t->warps_per_block > 8) {

@@ -64,7 +64,7 @@ __global__ void k_stepA_starts(const ExpT *__restrict__ exps, const uint64_t *__
 // At most 4 warps per block, 5 blocks per SM: 20 warps fit the register file
 // (<= 96 registers) and shared memory (9.6 KB per warp).
 template <int K, int VAR>
-__global__ void __launch_bounds__(128, 5) k_stepB(StepBJob J0, uint32_t n0, StepBJob J1, uint32_t n1)
+__global__ void __launch_bounds__(128, (K >= 16 ? 3 : K >= 12 ? 4 : 5)) k_stepB(StepBJob J0, uint32_t n0, StepBJob J1, uint32_t n1)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *sm = reinterpret_cast<WarpSmem *>(smem_raw);
@@ -142,6 +142,7 @@ static cudaError_t dispatch_k(int K, const StepBJob &J, uint32_t n0, const StepB
     case 2: return launch_b<2, VAR>(J, n0, J1, n1, wpb, st, occ);
     case 4: return launch_b<4, VAR>(J, n0, J1, n1, wpb, st, occ);
     case 8: return launch_b<8, VAR>(J, n0, J1, n1, wpb, st, occ);
+    case 12: return launch_b<12, VAR>(J, n0, J1, n1, wpb, st, occ);
     case 16: return launch_b<16, VAR>(J, n0, J1, n1, wpb, st, occ);
     default: return cudaErrorInvalidValue;
     }

@@ -80,7 +80,7 @@ extern "C" pe_status poly_eval_tune(pe_poly *P, uint64_t T, pe_tiles *best, doub
     bestE.ms = 1e300;
     pe_status result = PE_OK;
     for (int v : variants) {
-        for (uint32_t K : {1u, 2u, 4u, 8u, 16u}) {
+        for (uint32_t K : {1u, 2u, 4u, 8u, 12u, 16u}) {
             for (uint32_t wpb : {2u, 4u}) {
                 pe_tiles t{};
                 t.K = K;
@@ -241,7 +241,7 @@ extern "C" pe_status poly_eval_tune_load(const char *path)
         if (r == std::string::npos ||
             sscanf(line.c_str() + r, "\"K\": %u, \"wpb\": %u, \"variant\": %d, \"ms\": %lf", &K, &w, &v, &ms) != 4)
             continue;
-        if ((K != 1 && K != 2 && K != 4 && K != 8 && K != 16) || w < 1 || w > 8 || v < 1 || v > 4) continue;
+        if ((K != 1 && K != 2 && K != 4 && K != 8 && K != 12 && K != 16) || w < 1 || w > 8 || v < 1 || v > 4) continue;
         t.K = K;
         t.wpb = w;
         t.variant = v;

@@ -52,7 +52,7 @@ def test_tiny_config_all_variants():
         _check_full(w, v)
 
 
-@pytest.mark.parametrize("K", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("K", [1, 2, 4, 8, 12, 16])
 @pytest.mark.parametrize("variant", ["barrett64", "mont64"])
 def test_tile_shapes_zipf(K, variant):
     # Zipf groups: sizes from thousands of terms down to 1, so items cut groups
@@ -62,7 +62,7 @@ def test_tile_shapes_zipf(K, variant):
         _check_full(w, variant, dict(K=K, slabs=slabs, tchunk=tchunk, warps_per_block=2))
 
 
-@pytest.mark.parametrize("K", [1, 4, 8])
+@pytest.mark.parametrize("K", [1, 4, 8, 12])
 def test_fp64_variant(K):
     w = wl.make_zipf(n=6, s=20_000, p=P50, deg12=12, deg_rest=6, T=70, seed=6)
     _check_full(w, "fp64", dict(K=K, slabs=2, tchunk=45))
@@ -70,7 +70,7 @@ def test_fp64_variant(K):
     _check_full(w, "barrett64")
 
 
-@pytest.mark.parametrize("K", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("K", [1, 2, 4, 8, 12, 16])
 def test_barrett32_variant(K):
     # primes below 2^30 run the 32-bit product (the default for them)
     w = wl.make_zipf(n=7, s=25_000, p=P30, deg12=18, deg_rest=9, T=90, seed=25)
