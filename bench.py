@@ -47,8 +47,8 @@ NUM_SMS = 152
 # DRAM bytes (read + write) of one Step B launch on the large workload, from one
 # ncu capture of the current kernel with the item shape it ran; reported only
 # when the timed plan has that same shape (None for other workloads).
-STEPB_TRAFFIC_LARGE = {"bytes": 61_555_200 + 71_791_872,
-                       "shape": {"K": 8, "slabs": 1, "tchunk": 224, "warps_per_block": 4, "tail_points": 128}}
+STEPB_TRAFFIC_LARGE = {"bytes": 58_631_424 + 34_402_560,
+                       "shape": {"K": 16, "slabs": 1, "tchunk": 224, "warps_per_block": 4, "tail_points": 128}}
 
 
 def stepb_traffic(config, vkey, plan):
