@@ -721,7 +721,7 @@ def run_batched(args, print_line=True):
                        "term_points": tp, "terms": sum(w.s for w in ws), "jobs": len(ws),
                        "l2": "flushed between timed steps by a 256 MB device write"},
             "clocks": clk, "plain_loop": {"value": v_loop, "ms_per_step": statistics.mean(ms_loop),
-                                          "launches": sum(p.launches_per_run(w.T) for p, w in zip(polys, ws))},
+                                          "launches": launches_loop},
             "batched_over_plain_loop": v_batch / v_loop, "gpu_launches": 2 * args.steps,
             "host_seconds": {"generate": t_gen, "create": t_create, "plan_and_capture": t_plan}}
     print(json.dumps(line), flush=True)
