@@ -87,3 +87,26 @@ def test_tuner_picks_the_faster_method(tmp_path):
     assert poly.plan_info(w.T)["method"] == "matrix"
     assert np.array_equal(pe.to_u64(poly.run(w.beta, w.T)), plain)
     poly.close()
+
+
+def test_two_variables_one_group_and_shared_layout():
+    # n = 2: every monomial value is 1, so each image is the coefficient sums.
+    w = wl.make_uniform(n=2, s=3_000, p=P_NTT, deg12=3, deg_rest=0, T=130, seed=23)
+    _, ref = oracle.eval_direct(w)
+    poly = pe.Poly.from_workload(w)
+    assert np.array_equal(pe.to_u64(poly.run_fast(w.beta, w.T)), ref)
+    poly.close()
+    one = wl.make_uniform(n=5, s=9_000, p=P_NTT, deg12=0, deg_rest=6, T=300, seed=24)
+    _, ref = oracle.eval_direct(one)
+    poly = pe.Poly.from_workload(one)
+    assert poly.G == 1
+    assert np.array_equal(pe.to_u64(poly.run_fast(one.beta, one.T)), ref)
+    # the same terms modulo another NTT prime, sharing the exponents
+    p2 = wl.random_ntt_prime(50, 16, 704)
+    c2 = (one.coeffs % np.uint64(p2)).astype(np.uint64)
+    w2 = wl.Workload(p=p2, n=one.n, coeffs=c2, exps=one.exps, beta=one.beta % np.uint64(p2 - 2) + np.uint64(1),
+                     T=one.T, t0=1)
+    q = poly.like(p2, c2)
+    assert np.array_equal(pe.to_u64(q.run_fast(w2.beta, w2.T)), oracle.eval_direct(w2)[1])
+    q.close()
+    poly.close()
