@@ -373,13 +373,17 @@ void build_chunks(pe_poly *P, uint32_t K)
     h.cs.resize(nc + 1);
     h.cg.resize(nc);
     uint32_t *cs = h.cs.data(), *cg = h.cg.data();
-    for (uint64_t g = 0; g < P->G; ++g) {
-        uint64_t c = h.gfirst[g];
-        for (uint64_t st = P->group_off[g]; st < P->group_off[g + 1]; st += K, ++c) {
-            cs[c] = (uint32_t)st;
-            cg[c] = (uint32_t)g;
+    const unsigned nth = nc >= (1u << 15) ? 2 * host_pool_size() : 1u;
+    const std::function<void(unsigned)> fill = [&](unsigned t) {
+        for (uint64_t g = P->G * t / nth; g < P->G * (t + 1) / nth; ++g) {
+            uint64_t c = h.gfirst[g];
+            for (uint64_t st = P->group_off[g]; st < P->group_off[g + 1]; st += K, ++c) {
+                cs[c] = (uint32_t)st;
+                cg[c] = (uint32_t)g;
+            }
         }
-    }
+    };
+    host_parallel(nth, fill);
     cs[nc] = (uint32_t)P->s;
 }
 
