@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large",
-                    choices=["large", "large30", "tiny", "width62", "width62ntt", "width50", "batched", "served"])
+                    choices=["large", "large30", "tiny", "width62", "width62ntt", "width50", "batched", "served",
+                             "interp"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--tiles", default="",
                     help="force Step B tiles K,slabs,tchunk,warps_per_block,tail (no tuning), e.g. 16,1,224,4,128")
@@ -888,6 +889,13 @@ def main():
         run_batched(args)
     elif args.config == "served":
         print(json.dumps({"metric": "served", **run_served(args)}), flush=True)
+    elif args.config == "interp":
+        import torch
+        import paper_2004_11571_gb300 as pe
+        torch.cuda.set_device(0)
+        res = bench_interp(pe, torch, 2070.0, reps=max(args.steps, 1))
+        print(json.dumps({"metric": "interpolation from images (transposed Vandermonde solves)",
+                          "value": res[0]["terms_per_s"], "unit": "terms recovered/s", "cases": res}), flush=True)
     else:
         run_ours(args)
 
