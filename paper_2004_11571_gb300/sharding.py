@@ -9,8 +9,15 @@ of consecutive points and need no exchange on the data path.
   strong_block(T, t0, rank, world)   the T points t0..t0+T-1 split into
                                      world contiguous blocks (sizes differ by
                                      at most one point)
+  group_split(group_off, world)      contiguous ranges of (x1, x2) groups per
+                                     rank with about equal numbers of terms:
+                                     each rank owns whole output columns, so
+                                     again nothing is exchanged
+  job_split(costs, world)            independent jobs (a batch, a server's
+                                     requests) to ranks, largest first onto
+                                     the least loaded rank
 """
-from typing import Tuple
+from typing import List, Sequence, Tuple
 
 
 def weak_block(T: int, t0: int, rank: int) -> Tuple[int, int]:
@@ -27,3 +34,35 @@ def strong_block(T: int, t0: int, rank: int, world: int) -> Tuple[int, int]:
     base, extra = divmod(T, world)
     first = rank * base + min(rank, extra)
     return t0 + first, base + (1 if rank < extra else 0)
+
+
+def group_split(group_off: Sequence[int], world: int) -> List[Tuple[int, int]]:
+    """[(first group, end group)] per rank: contiguous group ranges whose term
+    counts are as even as whole groups allow (rank r ends at the first group
+    boundary at or past r+1 world-th of the terms)."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    G = len(group_off) - 1
+    s = int(group_off[-1]) if G >= 0 else 0
+    bounds, g = [0], 0
+    for r in range(1, world):
+        target = s * r // world
+        while g < G and int(group_off[g]) < target:
+            g += 1
+        bounds.append(max(g, bounds[-1]))
+    bounds.append(max(G, bounds[-1]))
+    return [(bounds[r], bounds[r + 1]) for r in range(world)]
+
+
+def job_split(costs: Sequence[float], world: int) -> List[List[int]]:
+    """Job indices per rank: longest-processing-time-first greedy, which keeps
+    the largest load within 4/3 of the best possible."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    load = [0.0] * world
+    out: List[List[int]] = [[] for _ in range(world)]
+    for j in sorted(range(len(costs)), key=lambda j: -costs[j]):
+        r = min(range(world), key=lambda r: load[r])
+        out[r].append(j)
+        load[r] += costs[j]
+    return out

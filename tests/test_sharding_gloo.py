@@ -1,7 +1,9 @@
-"""Multi-rank sharding of the points, run as world-size-2 gloo ranks on CPU.
+"""Multi-rank sharding, run as world-size-2 gloo ranks on CPU.
 
-Each rank evaluates its block of points with the oracle (no GPU here); the
-blocks are gathered over gloo and must equal one evaluation of all points.
+Each rank evaluates its share with the oracle (no GPU here): a block of the
+points, or a range of (x1, x2) groups (whole output columns); the shares are
+gathered over gloo and must equal one evaluation of everything.  Job splits
+for batches are checked for balance and coverage.
 """
 import os
 import socket
@@ -67,3 +69,48 @@ def test_blocks_partition_the_points():
     assert sharding.weak_block(64, 1, 3) == (193, 64)
     with pytest.raises(ValueError):
         sharding.strong_block(10, 1, 2, 2)
+
+
+def _group_rank_main(rank, world, port, result_path):
+    import oracle
+    import workloads as wl
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w = wl.make_zipf(n=6, s=4_000, p=wl.random_prime(62, 5), deg12=9, deg_rest=5, T=13, seed=6)
+    keys, tg = oracle.group_keys(w.exps)
+    off = np.concatenate([[0], np.cumsum(np.bincount(tg.astype(np.int64)))])
+    g0, g1 = sharding.group_split(off, world)[rank]
+    sub = wl.Workload(p=w.p, n=w.n, coeffs=w.coeffs[off[g0]:off[g1]], exps=w.exps[off[g0]:off[g1]],
+                      beta=w.beta, T=w.T, t0=1)
+    _, cols = oracle.eval_direct(sub)                       # this rank's output columns g0..g1-1
+    G = keys.shape[0]
+    full = torch.zeros((w.T, G), dtype=torch.int64)
+    full[:, g0:g1] = torch.from_numpy(cols.view(np.int64).copy())
+    dist.all_reduce(full)                                   # disjoint columns: the sum assembles them
+    if rank == 0:
+        _, ref = oracle.eval_direct(w)
+        np.save(result_path, np.array([np.array_equal(full.numpy().view(np.uint64), ref)]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_the_groups(tmp_path):
+    res = str(tmp_path / "ok.npy")
+    mp.start_processes(_group_rank_main, args=(2, _free_port(), res), nprocs=2, join=True, start_method="spawn")
+    assert bool(np.load(res)[0])
+
+
+def test_group_and_job_splits():
+    off = [0, 10, 11, 50, 51, 52, 100]
+    for world in (1, 2, 3, 8):
+        parts = sharding.group_split(off, world)
+        assert parts[0][0] == 0 and parts[-1][1] == 6
+        assert all(parts[r][1] == parts[r + 1][0] for r in range(world - 1))
+    assert sharding.group_split(off, 2) == [(0, 3), (3, 6)]
+    costs = [5.0, 1.0, 9.0, 3.0, 3.0, 7.0, 2.0]
+    split = sharding.job_split(costs, 3)
+    assert sorted(j for part in split for j in part) == list(range(len(costs)))
+    loads = [sum(costs[j] for j in part) for part in split]
+    assert max(loads) <= 4 / 3 * max(sum(costs) / 3, max(costs))
+    with pytest.raises(ValueError):
+        sharding.job_split(costs, 0)
