@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include "internal.h"
 #include "modarith.cuh"
@@ -210,6 +211,24 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
     std::vector<size_t> o_cs(njobs), o_cg(njobs), o_unit(njobs), o_span(njobs), o_carry(njobs), o_chain(njobs),
         o_ptab(njobs), o_cnt(njobs);
     img.beta_off.assign(njobs, 0);
+    // Power-table classes: (p, E, beta) -> leader; the class's table width is
+    // its largest dmax + 1 (Sect. 2.3 tables, computed once per class).
+    img.leader.resize(njobs);
+    std::vector<uint32_t> dp1c(njobs, 1);
+    {
+        std::map<std::vector<uint64_t>, size_t> cls;
+        for (size_t j = 0; j < njobs; ++j) {
+            img.leader[j] = j;
+            pe_poly *P = jobs[j].poly;
+            if (!jobs[j].T || !P->G || !P->E) continue;
+            std::vector<uint64_t> key{P->p, P->E};
+            key.insert(key.end(), img.betas[j].begin(), img.betas[j].end());
+            auto it = cls.emplace(key, j).first;
+            img.leader[j] = it->second;
+            dp1c[it->second] = std::max(dp1c[it->second], P->dmax + 1);
+        }
+        for (size_t j = 0; j < njobs; ++j) dp1c[j] = dp1c[img.leader[j]];
+    }
     for (size_t j = 0; j < njobs; ++j) {
         pe_poly *P = jobs[j].poly;
         if (!jobs[j].T || !P->G) continue;
@@ -225,7 +244,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
         img.beta_off[j] = U.take((size_t)std::max<uint32_t>(P->E, 1) * 8);
         o_carry[j] = S.take(ph[j].carry_bytes());
         o_chain[j] = S.take(ph[j].chain_bytes());
-        o_ptab[j] = S.take((size_t)std::max<uint32_t>(P->E, 1) * (P->dmax + 1) * 8);
+        o_ptab[j] = S.take((size_t)std::max<uint32_t>(P->E, 1) * dp1c[j] * 8);
     }
     // Items, ordered by decreasing cost (a slab-point of a K-term chunk costs K).
     std::vector<std::pair<double, uint2>> items;
@@ -279,19 +298,25 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
         put(o_unit[j], ph[j].unit.data(), ph[j].unit.size() * 4);
         put(o_span[j], ph[j].span.data(), ph[j].span.size() * 4);
         put(img.beta_off[j], img.betas[j].data(), img.betas[j].size() * 8);
+        const size_t lead = img.leader[j];
         fill_job(hj[j], P, ph[j], (const uint32_t *)(base + o_cs[j]), (const uint32_t *)(base + o_cg[j]),
                  (const int32_t *)(base + o_unit[j]), (const uint32_t *)(base + o_span[j]),
                  (uint32_t *)(base + o_cnt[j]), (ulonglong2 *)(base + o_carry[j]), (ulonglong2 *)(base + o_chain[j]),
-                 jb.t0, jb.out, nullptr, (const uint64_t *)(base + o_ptab[j]), var[j]);
+                 jb.t0, jb.out, nullptr, (const uint64_t *)(base + o_ptab[lead]), var[j]);
+        hj[j].dp1 = dp1c[j];
         hp[j].beta = (const uint64_t *)(base + img.beta_off[j]);
         hp[j].ptab = (uint64_t *)(base + o_ptab[j]);
-        hp[j].E = P->E;
-        hp[j].dp1 = P->dmax + 1;
+        hp[j].E = lead == j ? P->E : 0;   // followers read the leader's tables
+        hp[j].dp1 = dp1c[j];
         hp[j].mc = P->mc;
-        img.max_entries = std::max(img.max_entries, P->E * (P->dmax + 1));
+        if (lead == j) ++img.tables;
+        img.max_entries = std::max(img.max_entries, P->E * dp1c[j]);
     }
     put(off_jobs, hj.data(), njobs * sizeof(StepBJob));
     put(off_pow, hp.data(), njobs * sizeof(PowJob));
+    img.off_jobs = off_jobs;
+    img.off_pow = off_pow;
+    img.ptab_off = o_ptab;
     std::vector<uint2> it(items.size());
     for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
     put(off_items, it.data(), it.size() * sizeof(uint2));
@@ -408,10 +433,43 @@ extern "C" pe_status poly_eval_batch_set_beta(pe_batch *B, size_t j, const uint6
     if (st != PE_OK) return st;
     const uint32_t E = B->jobs[j].poly->E;
     if (!E) return PE_OK;
-    B->img.betas[j].assign(ba.b, ba.b + E);
-    cudaError_t e = cudaMemcpy(B->img.base + B->img.beta_off[j], B->img.betas[j].data(), E * 8,
-                               cudaMemcpyHostToDevice);
+    BatchImage &I = B->img;
+    I.betas[j].assign(ba.b, ba.b + E);
+    cudaError_t e = cudaMemcpy(I.base + I.beta_off[j], I.betas[j].data(), E * 8, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "beta upload");
+    if (!B->jobs[j].T || !B->jobs[j].poly->G) return PE_OK;
+    // A job that shared power tables leaves its class: it computes its own from
+    // now on, and if it led the class the next member takes over the lead.
+    const size_t lead = I.leader[j];
+    std::vector<size_t> members;
+    for (size_t k = 0; k < I.leader.size(); ++k)
+        if (I.leader[k] == lead && k != j) members.push_back(k);
+    if (members.empty()) return PE_OK;
+    auto job_at = [&](size_t k) { return (StepBJob *)(I.host.data() + I.off_jobs) + k; };
+    auto pow_at = [&](size_t k) { return (PowJob *)(I.host.data() + I.off_pow) + k; };
+    std::vector<size_t> touched{j};
+    I.leader[j] = j;
+    job_at(j)->ptab = (const uint64_t *)(I.base + I.ptab_off[j]);
+    pow_at(j)->E = E;
+    if (lead == j) {
+        const size_t nl = members[0];
+        pow_at(nl)->E = B->jobs[nl].poly->E;
+        for (size_t k : members) {
+            I.leader[k] = nl;
+            job_at(k)->ptab = (const uint64_t *)(I.base + I.ptab_off[nl]);
+            touched.push_back(k);
+        }
+    } else {
+        ++I.tables;
+    }
+    for (size_t k : touched) {
+        if ((e = cudaMemcpy(I.base + I.off_jobs + k * sizeof(StepBJob), job_at(k), sizeof(StepBJob),
+                            cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(I.base + I.off_pow + k * sizeof(PowJob), pow_at(k), sizeof(PowJob),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "batch descriptors");
+    }
+    if (lead == j) ++I.tables;
     return PE_OK;
 }
 

@@ -120,6 +120,13 @@ struct BatchImage {
     std::vector<unsigned char> host;          // bytes to upload at `base`
     std::vector<std::vector<uint64_t>> betas;
     std::vector<size_t> beta_off;
+    // Jobs with the same prime, number of variables and point share one set of
+    // power tables (the leader's); every job keeps a slot of its own so that
+    // poly_eval_batch_set_beta can split a job off.
+    std::vector<size_t> leader;               // per job: the job whose tables it reads
+    std::vector<size_t> ptab_off;             // per job: its own table slot (offset from base)
+    size_t off_jobs = 0, off_pow = 0;         // descriptor arrays (offsets from base)
+    uint32_t tables = 0;                      // power-table sets computed per launch
     unsigned char *base = nullptr;
     size_t counters_off = 0, counters_bytes = 0;
     StepBJob *d_jobs = nullptr;

@@ -125,3 +125,37 @@ def test_tuner_records_and_plain_uses_it(tmp_path):
     rnd = np.random.default_rng(0)
     r, g = rnd.integers(0, w.T, 16), rnd.integers(0, cells.G, 16)
     assert np.array_equal(got[r, g], cells(r + 1, g))
+
+
+def test_shared_power_tables_and_splitting_them():
+    """Jobs with the same prime and point share one set of power tables (the
+    paired evaluations of the gcd use, Sect. 2.2.2), with the table as wide as
+    the largest exponent among them; setting a new point for one job gives it
+    its own tables again, for a follower and for the leader."""
+    p = wl.random_prime(62, 321)
+    beta = np.random.default_rng(5).integers(2, p, size=4, dtype=np.uint64)
+    ws = [wl.make_uniform(n=6, s=2_000 + 500 * k, p=p, deg12=6, deg_rest=[3, 9, 5][k], T=40, seed=330 + k)
+          for k in range(3)]
+    for w in ws:
+        w.beta = beta.copy()
+    polys = [pe.Poly.from_workload(w) for w in ws]
+    outs = [torch.empty((w.T, q.G), dtype=torch.int64, device="cuda") for w, q in zip(ws, polys)]
+    batch = pe.Batch([(q, w.beta, w.T, 1, o) for q, w, o in zip(polys, ws, outs)])
+
+    def check():
+        batch.launch()
+        torch.cuda.synchronize()
+        for w, o in zip(ws, outs):
+            assert np.array_equal(pe.to_u64(o), oracle.eval_direct(w)[1])
+
+    check()                                              # one table set, width of the widest job (9)
+    rng = np.random.default_rng(6)
+    ws[2].beta = rng.integers(2, p, size=4, dtype=np.uint64)
+    batch.set_beta(2, ws[2].beta)                        # a follower leaves
+    check()
+    ws[0].beta = rng.integers(2, p, size=4, dtype=np.uint64)
+    batch.set_beta(0, ws[0].beta)                        # the leader leaves; job 1 leads alone
+    check()
+    batch.close()
+    for q in polys:
+        q.close()
