@@ -53,3 +53,34 @@ def test_binding_raises_without_library(monkeypatch):
     monkeypatch.setattr(pe, "LIB_PATH", "/nonexistent/libpolyeval.so")
     with pytest.raises(RuntimeError):
         pe.lib()
+
+
+def test_validation_of_later_entry_points(L):
+    """The interpolation solver, the fast method, multi-prime handles and the
+    monomial query check their arguments on the host before any device call."""
+    u64 = ctypes.c_uint64
+    p = (1 << 61) - 1
+    off = np.array([0, 2, 5], np.uint64)
+    dummy = ctypes.c_void_p(16)     # never dereferenced: every call below fails validation first
+    solve = L.poly_eval_vandermonde_solve
+    assert solve(p + 1, 2, off.ctypes.data, dummy, dummy, 5, 2, 1, dummy, None) == 2        # even modulus
+    assert solve(p, 2, None, dummy, dummy, 5, 2, 1, dummy, None) == 1                        # off missing
+    bad0 = np.array([1, 2, 5], np.uint64)
+    assert solve(p, 2, bad0.ctypes.data, dummy, dummy, 5, 2, 1, dummy, None) == 1           # off[0] != 0
+    down = np.array([0, 4, 3], np.uint64)
+    assert solve(p, 2, down.ctypes.data, dummy, dummy, 5, 2, 1, dummy, None) == 1           # decreasing
+    assert solve(p, 2, off.ctypes.data, dummy, dummy, 2, 2, 1, dummy, None) == 1            # rows < 3 terms
+    assert solve(p, 2, off.ctypes.data, dummy, dummy, 5, 1, 1, dummy, None) == 1            # lda < G
+    assert solve(p, 2, off.ctypes.data, None, dummy, 5, 2, 1, dummy, None) == 1             # z missing
+    assert b"device pointers" in L.poly_eval_last_error()
+    empty = np.array([0, 0, 0], np.uint64)
+    assert solve(p, 2, empty.ctypes.data, None, None, 0, 2, 1, None, None) == 0             # nothing to do
+    assert L.poly_eval_run_fast(None, None, 4, 1, dummy, None) == 1
+    assert L.poly_eval_monomials(None, None, dummy, None, None) == 1
+    h = ctypes.c_void_p()
+    assert L.poly_eval_create_like(None, p, dummy, 0, 0, ctypes.byref(h)) == 1
+    assert L.poly_eval_create_like(dummy, p, dummy, 0, 0, None) == 1
+    ms = (ctypes.c_double * 4)()
+    assert L.poly_eval_vandermonde_timing(-1, ms) == 0
+    nnz = u64()
+    assert L.poly_eval_compact(dummy, 1 << 32, 4, dummy, dummy, dummy, 0, ctypes.byref(nnz), None) == 1
