@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-stride", type=int, default=2)
+    ap.add_argument("--cpu-sample-stride", type=int, default=1)
     return ap.parse_args()
 
 
