@@ -183,6 +183,14 @@ void poly_eval_destroy(pe_poly *poly);
 const char *poly_eval_last_error(void);
 
 /*
+ * Testing aid for failure paths: the nth device allocation the library makes
+ * from now on (in any thread) fails as if the device were out of memory, and
+ * the call that made it returns PE_ERR_NOMEM; 0 cancels a pending failure.
+ * No GPU fault is involved; handles stay usable afterwards.
+ */
+pe_status poly_eval_debug_fail_alloc(uint32_t nth);
+
+/*
  * Tile shape of Step B.  A warp-lane owns a chunk of at most K consecutive
  * terms of one group and keeps their state in registers across a range of
  * points (the paper's dependent evaluations T_d, Sect. 4.1); 32 chunks form a

@@ -142,6 +142,7 @@ def lib():
             "poly_eval_monomials": (st, [_vp, _vp, _vp, _vp, _vp]),
             "poly_eval_create_like": (st, [_vp, _u64, _vp, _u32, ctypes.c_int, ctypes.POINTER(_vp)]),
             "poly_eval_run_fast": (st, [_vp, _vp, _u64, _u64, _vp, _vp]),
+            "poly_eval_debug_fail_alloc": (st, [_u32]),
             "poly_eval_vandermonde_solve": (st, [_u64, _u64, _vp, _vp, _vp, _u64, _u64, _u64, _vp, _vp]),
             "poly_eval_vandermonde_timing": (st, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         }
@@ -512,6 +513,12 @@ def vandermonde_timing(enable=None) -> dict:
     ms = (ctypes.c_double * 4)()
     _check(lib().poly_eval_vandermonde_timing(-1 if enable is None else int(bool(enable)), ms))
     return {"leaves": ms[0], "tree": ms[1], "correlation": ms[2], "horner": ms[3]}
+
+
+def debug_fail_alloc(nth: int):
+    """Make the nth device allocation of the library from now fail (0 cancels);
+    a testing aid for failure paths (poly_eval_debug_fail_alloc)."""
+    _check(lib().poly_eval_debug_fail_alloc(int(nth)))
 
 
 def int_pipe_rates() -> dict:

@@ -27,6 +27,17 @@ void set_error(const char *fmt, ...)
     g_err = buf;
 }
 
+// poly_eval_debug_fail_alloc: the countdown reaches 1 at the allocation that fails.
+static std::atomic<long> g_alloc_countdown{0};
+
+bool alloc_fault_now()
+{
+    long c = g_alloc_countdown.load(std::memory_order_relaxed);
+    while (c > 0 && !g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+    }
+    return c == 1;
+}
+
 pe_status cuda_fail(cudaError_t e, const char *what)
 {
     set_error("%s: %s", what, cudaGetErrorString(e));
@@ -689,6 +700,12 @@ static pe_status create_poly_device(const pe_poly_desc *d, int variant, pe_poly 
 using namespace pe;
 
 extern "C" const char *poly_eval_last_error(void) { return g_err.c_str(); }
+
+extern "C" pe_status poly_eval_debug_fail_alloc(uint32_t nth)
+{
+    g_alloc_countdown.store((long)nth);
+    return PE_OK;
+}
 
 extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out) { return create_poly(d, out, true); }
 

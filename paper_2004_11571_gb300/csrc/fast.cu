@@ -422,8 +422,8 @@ static pe_status fast_prepare(pe_poly *P, uint64_t T, cudaStream_t st)
     uint32_t logTp;
     fast_applicable(P->p, T, &logTp);
     const uint64_t p = P->p, Tp = 1ull << logTp, B = Tp;
-    F->T = T;
-    F->p = p;
+    F->T = 0;   // set once everything below has succeeded
+    F->p = 0;
     F->logTp = logTp;
     F->lognmax = logTp + 1;
     // Blocks of at most B terms per group; chunks of 32 within blocks; pairs per level.
@@ -514,6 +514,8 @@ static pe_status fast_prepare(pe_poly *P, uint64_t T, cudaStream_t st)
         (err = cudaMemcpyAsync(F->tables.p, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (err = cudaMemcpyAsync(F->gblk.p, gblk.data(), gblk.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(err, "fast method upload");
+    F->T = T;
+    F->p = p;
     return PE_OK;
 }
 

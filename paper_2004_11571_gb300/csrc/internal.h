@@ -23,6 +23,10 @@ pe_status cuda_fail(cudaError_t e, const char *what);
 // completed epochs released.
 cudaStream_t alloc_stream();
 
+// Testing aid (poly_eval_debug_fail_alloc): true when this device
+// allocation is the one chosen to fail.
+bool alloc_fault_now();
+
 // Owned device allocation that only grows.
 struct DevBuf {
     void *p = nullptr;
@@ -44,6 +48,7 @@ struct DevBuf {
         if (n <= bytes && p) return cudaSuccess;
         release();
         if (n == 0) n = 16;
+        if (alloc_fault_now()) return cudaErrorMemoryAllocation;
         if (!s) s = alloc_stream();
         cudaError_t e = cudaMallocAsync(&p, n, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -61,6 +66,7 @@ struct DevBuf {
         if (n <= bytes && p) return cudaSuccess;
         release();
         if (n == 0) n = 16;
+        if (alloc_fault_now()) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMallocAsync(&p, n, s);
         if (e != cudaSuccess) {
             p = nullptr;
