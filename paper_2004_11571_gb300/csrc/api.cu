@@ -245,15 +245,40 @@ void host_parallel(unsigned n, const std::function<void(unsigned)> &fn)
 
 unsigned host_pool_size() { return (unsigned)host_pool().threads.size() + 1; }
 
+static constexpr int kMaxDevices = 64;
+
 int num_sms()
 {
-    static int n = 0;
+    static std::atomic<int> cached[kMaxDevices] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kMaxDevices) dev = 0;
+    int n = cached[dev].load(std::memory_order_relaxed);
     if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        cached[dev].store(n, std::memory_order_relaxed);
     }
     return n;
+}
+
+cudaError_t smem_limit_once(const void *func, int bytes)
+{
+    // (function, device) pairs already raised; a concurrent first call raises it twice, which is harmless
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        for (const auto &d : done)
+            if (d.first == func && d.second == dev) return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    done.emplace_back(func, dev);
+    return cudaSuccess;
 }
 
 pe_status check_beta(const pe_poly *poly, const uint64_t *beta, BetaArg *arg)

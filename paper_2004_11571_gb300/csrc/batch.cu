@@ -103,13 +103,8 @@ static size_t queue_smem() { return kQueueWarps * sizeof(QueueSmem); }
 
 static cudaError_t queue_setup(int *blocks_per_sm)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_stepB_queue, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)queue_smem());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = smem_limit_once((const void *)k_stepB_queue, (int)queue_smem());
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_stepB_queue, kQueueWarps * 32,
                                                          queue_smem());
 }

@@ -23,6 +23,10 @@ struct ModCtx {
 
 ModCtx make_modctx(uint64_t p);  // host
 
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per device (thread-safe; the attribute is per device).
+cudaError_t smem_limit_once(const void *func, int bytes);
+
 struct BetaArg {
     uint64_t b[kMaxEval];
 };

@@ -580,12 +580,9 @@ extern "C" pe_status poly_eval_run_fast(pe_poly *P, const uint64_t *beta, uint64
     uint64_t *Nbuf[2] = {F.N0.as<uint64_t>(), F.N1.as<uint64_t>()};
     k_fast_leaf<<<(F.nchunks + 3) / 4, 128, 0, cs>>>(chunks, F.nchunks, P->mR.as<uint64_t>(), P->coeffs.as<uint64_t>(),
                                                      t0, P->mc, r2, Dbuf[0], Nbuf[0]);
-    static int smem_set = 0;
-    if (!smem_set) {
-        cudaFuncSetAttribute(k_fast_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 2 * kFastMaxT / 2 * 8);
-        cudaFuncSetAttribute(k_fast_series, cudaFuncAttributeMaxDynamicSharedMemorySize, 5 * kFastMaxT * 8);
-        smem_set = 1;
-    }
+    if ((e = smem_limit_once((const void *)k_fast_merge, 4 * 2 * kFastMaxT / 2 * 8)) != cudaSuccess ||
+        (e = smem_limit_once((const void *)k_fast_series, 5 * kFastMaxT * 8)) != cudaSuccess)
+        return cuda_fail(e, "fast method shared memory");
     for (size_t lv = 0; lv < F.level_count.size(); ++lv) {
         if (!F.level_count[lv]) continue;   // no block reaches this level (the buffers' roles still alternate)
         const uint32_t logL = 5 + (uint32_t)lv, L = 1u << logL;

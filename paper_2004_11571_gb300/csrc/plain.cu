@@ -119,13 +119,9 @@ static cudaError_t launch_b(const StepBJob &J, uint32_t nitems, const StepBJob &
                            cudaStream_t st, int *occ)
 {
     const size_t smem = (size_t)wpb * sizeof(WarpSmem);
-    static bool attr_set = false;   // once, at the largest block (8 warps)
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_stepB<K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kMaxStepBWarps * sizeof(WarpSmem)));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    // once per device, at the largest block (8 warps)
+    cudaError_t e = smem_limit_once((const void *)k_stepB<K, VAR>, (int)(kMaxStepBWarps * sizeof(WarpSmem)));
+    if (e != cudaSuccess) return e;
     if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_stepB<K, VAR>, wpb * 32, smem);
     if (nitems + n1 == 0) return cudaSuccess;
     const uint32_t grid = (nitems + n1 + wpb - 1) / wpb;
