@@ -145,6 +145,7 @@ def lib():
             "poly_eval_debug_fail_alloc": (st, [_u32]),
             "poly_eval_vandermonde_solve": (st, [_u64, _u64, _vp, _vp, _vp, _u64, _u64, _u64, _vp, _vp]),
             "poly_eval_vandermonde_timing": (st, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+            "poly_eval_stepb_noalloc": (st, [_u64, _u64, _u64, _vp, _vp, _vp, _u64, _u64, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -459,8 +460,6 @@ def stepb_noalloc(p: int, coeffs, m, group_off, T: int, t0: int, out, stream=Non
     uint64), group_off (int32 view of uint32, G+1 entries) and out (T x G)."""
     L = lib()
     fn = L.poly_eval_stepb_noalloc
-    fn.restype = ctypes.c_int
-    fn.argtypes = [_u64, _u64, _u64, _vp, _vp, _vp, _u64, _u64, _vp, _vp]
     s, G = int(coeffs.shape[0]), int(group_off.shape[0]) - 1
     _check(fn(int(p), s, G, coeffs.data_ptr(), m.data_ptr(), group_off.data_ptr(), int(T), int(t0),
               out.data_ptr(), _stream_ptr(stream)))

@@ -281,6 +281,19 @@ cudaError_t smem_limit_once(const void *func, int bytes)
     return cudaSuccess;
 }
 
+bool points_ok(uint64_t T, uint64_t t0)
+{
+    if (T > (1ull << 31)) {
+        set_error("T above 2^31");
+        return false;
+    }
+    if (T && t0 > ~0ull - (T - 1)) {
+        set_error("the last point t0 + T - 1 is above 2^64 - 1");
+        return false;
+    }
+    return true;
+}
+
 pe_status check_beta(const pe_poly *poly, const uint64_t *beta, BetaArg *arg)
 {
     memset(arg, 0, sizeof *arg);
@@ -1173,10 +1186,7 @@ pe_status pe::run_matrix(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t 
         set_error("NULL poly");
         return PE_ERR_ARG;
     }
-    if (T > (1ull << 31)) {
-        set_error("T above 2^31");
-        return PE_ERR_ARG;
-    }
+    if (!points_ok(T, t0)) return PE_ERR_ARG;
     BetaArg barg;
     pe_status st = check_beta(P, beta, &barg);
     if (st != PE_OK) return st;

@@ -183,10 +183,11 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
     double w_total = 0.0;
     for (size_t j = 0; j < njobs; ++j) {
         const pe_job &jb = jobs[j];
-        if (!jb.poly || (jb.T && jb.poly->G && !jb.out) || jb.T > (1ull << 31)) {
-            set_error("job %zu: NULL poly/out or T above 2^31", j);
+        if (!jb.poly || (jb.T && jb.poly->G && !jb.out)) {
+            set_error("job %zu: NULL poly or out", j);
             return PE_ERR_ARG;
         }
+        if (!points_ok(jb.T, jb.t0)) return PE_ERR_ARG;
         BetaArg ba;
         pe_status st = check_beta(jb.poly, jb.beta, &ba);
         if (st != PE_OK) return st;

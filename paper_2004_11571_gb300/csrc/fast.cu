@@ -534,6 +534,7 @@ extern "C" pe_status poly_eval_run_fast(pe_poly *P, const uint64_t *beta, uint64
         set_error("the fast method takes T <= %u", kFastMaxT);
         return PE_ERR_ARG;
     }
+    if (!points_ok(T, t0)) return PE_ERR_ARG;
     if (T == 0 || P->G == 0) return PE_OK;
     if (!fast_applicable(P->p, T, &logTp)) {
         set_error("the fast method needs p - 1 divisible by %llu (NTTs of twice the padded T)",

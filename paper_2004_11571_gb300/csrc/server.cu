@@ -411,10 +411,7 @@ extern "C" pe_status poly_eval_server_submit(pe_server *S, const pe_request *req
         set_error("bad request");
         return PE_ERR_ARG;
     }
-    if (req->T > (1ull << 31)) {
-        set_error("T above 2^31");
-        return PE_ERR_ARG;
-    }
+    if (!points_ok(req->T, req->t0)) return PE_ERR_ARG;
     SrvRequest *r = new SrvRequest();
     r->resident_id = req->resident_id;
     r->T = req->T;

@@ -84,3 +84,18 @@ def test_validation_of_later_entry_points(L):
     assert L.poly_eval_vandermonde_timing(-1, ms) == 0
     nnz = u64()
     assert L.poly_eval_compact(dummy, 1 << 32, 4, dummy, dummy, dummy, 0, ctypes.byref(nnz), None) == 1
+
+
+def test_points_must_fit_in_64_bits(L):
+    """T <= 2^31 and the last point t0 + T - 1 below 2^64, checked before any
+    pointer is looked at (the pointers below are never dereferenced)."""
+    p = (1 << 61) - 1
+    dummy = ctypes.c_void_p(16)
+    na = L.poly_eval_stepb_noalloc
+    top = (1 << 64) - 1
+    assert na(p, 1, 1, dummy, dummy, dummy, 2, top, dummy, None) == 1          # t0 + 1 wraps
+    assert na(p, 1, 1, dummy, dummy, dummy, 2, top - 2, dummy, None) == 1      # t0 + T - 1 fits: the
+    assert b"device pointers" in L.poly_eval_last_error()                     # pointer check comes next
+    assert na(p, 1, 1, dummy, dummy, dummy, (1 << 31) + 1, 1, dummy, None) == 1
+    assert b"2^31" in L.poly_eval_last_error()
+    assert na(p, 1, 1, dummy, dummy, dummy, 0, top, dummy, None) == 0         # no points: nothing to do
