@@ -281,6 +281,28 @@ cudaError_t smem_limit_once(const void *func, int bytes)
     return cudaSuccess;
 }
 
+bool plan_start_gaps(StartRows *sr)
+{
+    sr->ngap = 0;
+    sr->gap_hb = 0;
+    for (int j = 0; j < kMaxGaps; ++j) sr->gap[j] = 0;   // unused entries have no bits
+    uint32_t bits = 0;
+    for (uint32_t k = 1; k < sr->n; ++k) {
+        const uint32_t g = sr->row[k] - sr->row[k - 1];
+        if (g == 0) return false;                   // rows must increase
+        uint32_t j = 0;
+        while (j < sr->ngap && sr->gap[j] != g) ++j;
+        if (j == sr->ngap) {
+            if (sr->ngap == (uint32_t)kMaxGaps) return false;
+            sr->gap[sr->ngap++] = g;
+        }
+        sr->gidx[k] = (uint8_t)j;
+        bits |= g;
+    }
+    while (bits >> (sr->gap_hb + 1)) ++sr->gap_hb;
+    return true;
+}
+
 bool points_ok(uint64_t T, uint64_t t0)
 {
     if (T > (1ull << 31)) {
@@ -1238,10 +1260,13 @@ pe_status pe::run_matrix(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t 
     const uint64_t T0 = T - t.tailT;
     StartRows sr{};
     const uint32_t q0 = P->plan.Q, q1 = t.tailT ? P->tail_plan.Q : 0;
-    const bool use_starts = q0 + q1 <= (uint32_t)kMaxStarts;
+    bool use_starts = q0 + q1 <= (uint32_t)kMaxStarts;
     if (use_starts) {
         for (uint32_t q = 0; q < q0; ++q) sr.row[sr.n++] = q * P->plan.Tc;
         for (uint32_t q = 0; q < q1; ++q) sr.row[sr.n++] = (uint32_t)T0 + q * P->tail_plan.Tc;
+        use_starts = plan_start_gaps(&sr);   // at most three distinct gaps (main band, band change, tail band)
+    }
+    if (use_starts) {
         if ((e = P->vstart.ensure_async((size_t)sr.n * P->s * 8, cs)) != cudaSuccess) return cuda_fail(e, "start values");
         e = launch_stepA_starts(P->exps->p, P->exp_bytes, P->coeffs.as<uint64_t>(), P->s, P->E,
                                 P->ptab.as<uint64_t>(), dp1, P->mc, t0, sr, P->mR.as<uint64_t>(),

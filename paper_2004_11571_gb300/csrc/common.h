@@ -55,11 +55,18 @@ struct StepBJob {
 };
 
 constexpr int kMaxStarts = 128;
+constexpr int kMaxGaps = 4;
 
-// Start rows (offsets from t0) of the work items of a plain run.
+// Start rows (offsets from t0) of the work items of a plain run, strictly
+// increasing, and the distinct gaps between consecutive rows: row k follows
+// row k-1 by gap[gidx[k]]; entries of gap past ngap are 0; gap_hb is the
+// highest bit set in any gap.
 struct StartRows {
     uint32_t n;
     uint32_t row[kMaxStarts];
+    uint32_t ngap, gap_hb;
+    uint32_t gap[kMaxGaps];
+    uint8_t gidx[kMaxStarts];
 };
 
 }  // namespace pe

@@ -198,6 +198,10 @@ int num_sms();
 // The points t0 .. t0+T-1 must be representable: T <= 2^31 and t0 + T - 1 < 2^64.
 // Sets the error message and returns false otherwise.
 bool points_ok(uint64_t T, uint64_t t0);
+
+// Fills the distinct-gap fields of the start rows (row[0..n) already set);
+// false if the rows do not increase or have more than kMaxGaps distinct gaps.
+bool plan_start_gaps(StartRows *sr);
 // Chooses the tile shape for a run of T points (forced fields win).
 Tiles choose_tiles(pe_poly *poly, uint64_t T, const pe_tiles *forced);
 // Builds (or reuses) `pl` for the given tiles and T.

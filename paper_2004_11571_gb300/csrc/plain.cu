@@ -31,8 +31,10 @@ __global__ void k_stepA(const ExpT *__restrict__ exps, uint64_t s, uint32_t E, c
 
 // Step A with starting values: besides m_i, every term's value a_i * m_i^t
 // at each work-item start row t = t0 + row[k], so that Step B items start
-// with one load.  Consecutive rows are reached by multiplying by m_i^gap,
-// with m_i^gap recomputed only when the gap changes.
+// with one load.  Consecutive rows are reached by multiplying by m_i^gap; the
+// powers for the (at most kMaxGaps) distinct gaps come from one chain of
+// squarings m_i^(2^b), b <= the highest gap bit, shared by all of them (the
+// gaps are the same for every term, so the branches are uniform).
 template <typename ExpT>
 __global__ void k_stepA_starts(const ExpT *__restrict__ exps, const uint64_t *__restrict__ coeffs, uint64_t s,
                                uint32_t E, const uint64_t *__restrict__ ptab, uint32_t dp1, ModCtx mc, uint64_t t0,
@@ -43,15 +45,21 @@ __global__ void k_stepA_starts(const ExpT *__restrict__ exps, const uint64_t *__
         mR_out[i] = mR;
         uint64_t cur = canon(mont_mul(coeffs[i], mont_pow(mR, t0 + sr.row[0], mc), mc), mc.p);
         vstart[i] = cur;
-        uint32_t prev_gap = 0;
-        uint64_t gapR = mc.r1;
+        uint64_t gp[kMaxGaps];
+#pragma unroll
+        for (int j = 0; j < kMaxGaps; ++j) gp[j] = 0;
+        uint64_t sq = mR;
+        for (uint32_t b = 0; b <= sr.gap_hb; ++b) {
+#pragma unroll
+            for (int j = 0; j < kMaxGaps; ++j)
+                if ((sr.gap[j] >> b) & 1)   // the lowest set bit starts the product, later ones multiply
+                    gp[j] = (sr.gap[j] & ((1u << b) - 1)) ? mont_mul(gp[j], sq, mc) : sq;
+            if (b < sr.gap_hb) sq = mont_mul(sq, sq, mc);
+        }
         for (uint32_t k = 1; k < sr.n; ++k) {
-            const uint32_t gap = sr.row[k] - sr.row[k - 1];
-            if (gap != prev_gap) {
-                gapR = mont_pow(mR, gap, mc);
-                prev_gap = gap;
-            }
-            cur = canon(mont_mul(cur, gapR, mc), mc.p);
+            const uint32_t gi = sr.gidx[k];
+            const uint64_t g = gi == 0 ? gp[0] : gi == 1 ? gp[1] : gi == 2 ? gp[2] : gp[3];
+            cur = canon(mont_mul(cur, g, mc), mc.p);
             vstart[(uint64_t)k * s + i] = cur;
         }
     }
