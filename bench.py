@@ -12,7 +12,9 @@ The metric is term-point evaluations per second (s*T per step).
            host arrays (upload), run into pinned host memory (download), destroy
   roofline Step B, timed live with events on its stream, against the integer
            multiply issue rate of the SMs at the sampled SM clock
-  cpu_baseline  the oracle's Algorithm 1 (single thread) on a sample of groups
+  cpu_baseline  the oracle's Algorithm 1 (single thread) over the workload; also
+           the oracle's plain definition on 1/64 of the groups and Algorithm 1
+           on every host core
 
 --impl reference times the oracle instead (the method's plain CPU statement).
 Under torchrun each rank evaluates its own block of T points (weak scaling,
@@ -172,6 +174,22 @@ def cpu_baseline(w, stride):
     dt = time.perf_counter() - t
     return {"value": sub.term_points / dt, "unit": "term-points/s", "cores": 1, "kind": "oracle",
             "sample": f"Algorithm 1 of the oracle (gcc -O2, unsigned __int128) on every {stride}-th group: "
+                      f"{sub.s} terms x {w.T} points = {sub.term_points:.3e} term-points in {dt:.1f} s",
+            "seconds": dt}
+
+
+def cpu_baseline_direct(w, stride=64):
+    """The oracle's plain definition (one thread: every point's powers of beta,
+    then each term's product of them) on every `stride`-th group, all T points."""
+    import oracle
+    keys, tg = oracle.group_keys(w.exps)
+    sel = (tg % stride) == 0
+    sub = wl.Workload(p=w.p, n=w.n, coeffs=w.coeffs[sel], exps=w.exps[sel], beta=w.beta, T=w.T, t0=w.t0)
+    t = time.perf_counter()
+    oracle.eval_direct(sub)
+    dt = time.perf_counter() - t
+    return {"value": sub.term_points / dt, "unit": "term-points/s", "cores": 1, "kind": "oracle (definition)",
+            "sample": f"the definition in the oracle (gcc -O2, unsigned __int128) on every {stride}-th group: "
                       f"{sub.s} terms x {w.T} points = {sub.term_points:.3e} term-points in {dt:.1f} s",
             "seconds": dt}
 
@@ -629,6 +647,7 @@ def run_ours(args):
             "roofline": roof}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_stride)
+        line["cpu_baseline_definition"] = cpu_baseline_direct(w)
         if args.config in ("large", "large30", "tiny"):
             line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.config)
     if world == 1 and not args.no_extras:
