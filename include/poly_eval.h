@@ -147,8 +147,8 @@ pe_status poly_eval_groups(const pe_poly *poly, uint64_t *G, uint32_t *keys);
 /*
  * Evaluates the T bivariate images b_t = f(x1, x2, beta^t), t = t0..t0+T-1
  * (Sect. 2.1; t0 = 1 avoids the unlucky point beta^0, t0 = 0 is allowed).
- *   T    : at most 2^31 points, the last of them t0 + T - 1 below 2^64
- *          (else PE_ERR_ARG); T = 0 does nothing.
+ *   T    : at most 2^31 points, the last of them t0 + T - 1 below 2^64, and
+ *          T x G at most 2^60 values (else PE_ERR_ARG); T = 0 does nothing.
  *   beta : host array of n-2 values, each in [1, p).
  *   out  : T x G uint64 (layout above), host or device memory.  With a device
  *          pointer the call is asynchronous on `stream`; with a host pointer it

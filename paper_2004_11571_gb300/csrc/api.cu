@@ -303,6 +303,15 @@ bool plan_start_gaps(StartRows *sr)
     return true;
 }
 
+bool out_ok(uint64_t T, uint64_t G)
+{
+    if (G && T > (1ull << 60) / G) {
+        set_error("the output of %llu x %llu values is above 2^60", (unsigned long long)T, (unsigned long long)G);
+        return false;
+    }
+    return true;
+}
+
 bool points_ok(uint64_t T, uint64_t t0)
 {
     if (T > (1ull << 31)) {
@@ -1208,7 +1217,7 @@ pe_status pe::run_matrix(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t 
         set_error("NULL poly");
         return PE_ERR_ARG;
     }
-    if (!points_ok(T, t0)) return PE_ERR_ARG;
+    if (!points_ok(T, t0) || !out_ok(T, P->G)) return PE_ERR_ARG;
     BetaArg barg;
     pe_status st = check_beta(P, beta, &barg);
     if (st != PE_OK) return st;

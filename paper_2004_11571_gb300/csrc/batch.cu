@@ -187,7 +187,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
             set_error("job %zu: NULL poly or out", j);
             return PE_ERR_ARG;
         }
-        if (!points_ok(jb.T, jb.t0)) return PE_ERR_ARG;
+        if (!points_ok(jb.T, jb.t0) || !out_ok(jb.T, jb.poly->G)) return PE_ERR_ARG;
         BetaArg ba;
         pe_status st = check_beta(jb.poly, jb.beta, &ba);
         if (st != PE_OK) return st;

@@ -199,6 +199,10 @@ int num_sms();
 // Sets the error message and returns false otherwise.
 bool points_ok(uint64_t T, uint64_t t0);
 
+// The T x G output must hold at most 2^60 values (its byte count fits in 64
+// bits with room to spare).  Sets the error message and returns false otherwise.
+bool out_ok(uint64_t T, uint64_t G);
+
 // Fills the distinct-gap fields of the start rows (row[0..n) already set);
 // false if the rows do not increase or have more than kMaxGaps distinct gaps.
 bool plan_start_gaps(StartRows *sr);

@@ -222,7 +222,7 @@ extern "C" pe_status poly_eval_stepb_noalloc(uint64_t p, uint64_t s, uint64_t G,
         set_error("p must be odd, at least 3 and below 2^62");
         return PE_ERR_PRIME;
     }
-    if (!points_ok(T, t0)) return PE_ERR_ARG;
+    if (!points_ok(T, t0) || !out_ok(T, G)) return PE_ERR_ARG;
     if (T == 0 || s == 0) return PE_OK;
     if (G == 0 || G > s || s >= 0xffffffffull) {
         set_error("sizes out of range (need 1 <= G <= s < 2^32 - 1, T <= 2^31)");

@@ -179,7 +179,12 @@ struct pe_server {
                 r->desc.exps = r->exps.data();
             }
             pe_poly *P = nullptr;
-            const pe_status st = create_poly(&r->desc, &P, false);
+            pe_status st = create_poly(&r->desc, &P, false);
+            if (st == PE_OK && !out_ok(r->T, P->G)) {   // its output could not be addressed
+                poly_eval_destroy(P);
+                P = nullptr;
+                st = PE_ERR_ARG;
+            }
             std::vector<uint8_t>().swap(r->exps);
             std::vector<uint64_t>().swap(r->coeffs);
             const double dt = since(t0);
@@ -446,6 +451,10 @@ extern "C" pe_status poly_eval_server_submit(pe_server *S, const pe_request *req
             return PE_ERR_NOT_FOUND;
         }
         n = it->second.poly->n;
+        if (!out_ok(req->T, it->second.poly->G)) {
+            delete r;
+            return PE_ERR_ARG;
+        }
     }
     if (n > 2 && !req->beta) {
         delete r;

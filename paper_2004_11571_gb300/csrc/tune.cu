@@ -60,6 +60,7 @@ extern "C" pe_status poly_eval_tune(pe_poly *P, uint64_t T, pe_tiles *best, doub
         set_error("empty polynomial");
         return PE_ERR_ARG;
     }
+    if (!points_ok(T, 1) || !out_ok(T, P->G)) return PE_ERR_ARG;
     std::vector<uint64_t> beta(std::max<uint32_t>(P->E, 1));
     for (size_t j = 0; j < beta.size(); ++j) beta[j] = 2 + (j * 7919) % (P->p - 3);
     DevBuf out;

@@ -99,3 +99,5 @@ def test_points_must_fit_in_64_bits(L):
     assert na(p, 1, 1, dummy, dummy, dummy, (1 << 31) + 1, 1, dummy, None) == 1
     assert b"2^31" in L.poly_eval_last_error()
     assert na(p, 1, 1, dummy, dummy, dummy, 0, top, dummy, None) == 0         # no points: nothing to do
+    assert na(p, 1 << 31, 1 << 31, dummy, dummy, dummy, 1 << 31, 1, dummy, None) == 1   # 2^62 output values
+    assert b"2^60" in L.poly_eval_last_error()
