@@ -720,6 +720,7 @@ def run_batched(args, print_line=True):
     v_batch = tp / (statistics.mean(ms_batch) * 1e-3)
     v_loop = tp / (statistics.mean(ms_loop) * 1e-3)
     launches_loop = sum(p.launches_per_run(w.T) for p, w in zip(polys, ws))
+    bl = batch.launches()
     batch.close()
     for p in polys:
         p.close()
@@ -729,8 +730,8 @@ def run_batched(args, print_line=True):
                            "T in {64,256,1024,2048}, 50/62-bit primes",
                "term_points": tp, "batched_term_points_per_s": v_batch, "ms_per_launch": statistics.mean(ms_batch),
                "plain_loop_term_points_per_s": v_loop, "plain_loop_ms": statistics.mean(ms_loop),
-               "batched_over_plain_loop": v_batch / v_loop, "launches_batched": 3,
-               "launches_plain_loop": launches_loop}
+               "batched_over_plain_loop": v_batch / v_loop, "launches_batched": bl["kernels"],
+               "plain_run_jobs": bl["plain_jobs"], "launches_plain_loop": launches_loop}
     if not print_line:
         return summary
     line = {"metric": "term-point evaluations/s (batched)", "value": v_batch * world, "unit": "term-points/s",
@@ -742,7 +743,7 @@ def run_batched(args, print_line=True):
                        "l2": "flushed between timed steps by a 256 MB device write"},
             "clocks": clk, "plain_loop": {"value": v_loop, "ms_per_step": statistics.mean(ms_loop),
                                           "launches": launches_loop},
-            "batched_over_plain_loop": v_batch / v_loop, "gpu_launches": 2 * args.steps,
+            "batched_over_plain_loop": v_batch / v_loop, "gpu_launches": bl["kernels"] * args.steps,
             "host_seconds": {"generate": t_gen, "create": t_create, "plan_and_capture": t_plan}}
     print(json.dumps(line), flush=True)
     return summary

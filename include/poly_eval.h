@@ -343,12 +343,22 @@ typedef struct pe_batch pe_batch;
  * Plans a batch: per-job tiles (from the autotuner cache when present),
  * a work queue ordered by decreasing cost, and a CUDA graph of the batch
  * (power tables for every job, then one persistent kernel that runs Step A
- * fused into Step B for every work item).  Job descriptors are copied.
+ * fused into Step B for every work item).  Jobs of at least 2^28
+ * term-points (s*T) fill the GPU on their own: they are left out of the
+ * graph and run as plain runs (poly_eval_run's matrix method, with the
+ * handle's scratch) after it.  Job descriptors are copied.
  */
 pe_status poly_eval_batch_plan(const pe_job *jobs, size_t njobs, pe_batch **out);
 
-/* Launches the planned batch's CUDA graph on `stream` (asynchronous). */
+/* Launches the planned batch's CUDA graph on `stream`, then its plain runs
+ * (asynchronous; the handles of plain runs must not be run elsewhere
+ * meanwhile, as for poly_eval_run). */
 pe_status poly_eval_batch_launch(pe_batch *batch, void *stream);
+
+/* Kernel launches per poly_eval_batch_launch (the graph's and the plain
+ * runs') and the number of jobs that run as plain runs; either pointer may
+ * be NULL. */
+pe_status poly_eval_batch_launches(const pe_batch *batch, uint32_t *kernels, uint32_t *plain_jobs);
 
 /* Replaces the beta values of job `j` for later launches (same T and t0). */
 pe_status poly_eval_batch_set_beta(pe_batch *batch, size_t j, const uint64_t *beta);

@@ -123,6 +123,7 @@ def lib():
             "poly_eval_batch_plan": (st, [_vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
             "poly_eval_batch_launch": (st, [_vp, _vp]),
             "poly_eval_batch_set_beta": (st, [_vp, ctypes.c_size_t, _vp]),
+            "poly_eval_batch_launches": (st, [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
             "poly_eval_batch_destroy": (None, [_vp]),
             "poly_eval_batch": (st, [_vp, ctypes.c_size_t, _vp]),
             "poly_eval_tune": (st, [_vp, _u64, ctypes.POINTER(_Tiles), ctypes.POINTER(ctypes.c_double)]),
@@ -329,7 +330,8 @@ class Poly:
 
 class Batch:
     """A planned batch (poly_eval_batch_plan): one CUDA graph running every job's
-    power tables and a persistent Step A+B kernel over a shared work queue.
+    power tables and a persistent Step A+B kernel over a shared work queue;
+    jobs of at least 2^28 term-points run as plain runs after it.
 
     jobs: sequence of (poly, beta, T, t0, out) with `out` a CUDA tensor (T x G)."""
 
@@ -354,6 +356,12 @@ class Batch:
     def set_beta(self, j: int, beta):
         b = np.ascontiguousarray(np.asarray(beta, dtype=np.uint64).reshape(-1))
         _check(lib().poly_eval_batch_set_beta(self._h, int(j), b.ctypes.data if b.size else None))
+
+    def launches(self) -> dict:
+        """Kernel launches per launch() and the number of plain-run jobs."""
+        k, n = _u32(), _u32()
+        _check(lib().poly_eval_batch_launches(self._h, ctypes.byref(k), ctypes.byref(n)))
+        return {"kernels": k.value, "plain_jobs": n.value}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -180,7 +180,8 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
         return PE_ERR_ARG;
     }
     img.betas.resize(njobs);
-    double w_total = 0.0;
+    img.is_plain.assign(njobs, 0);
+    double w_total = 0.0, w_queue = 0.0;
     for (size_t j = 0; j < njobs; ++j) {
         const pe_job &jb = jobs[j];
         if (!jb.poly || (jb.T && jb.poly->G && !jb.out)) {
@@ -192,10 +193,19 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
         pe_status st = check_beta(jb.poly, jb.beta, &ba);
         if (st != PE_OK) return st;
         img.betas[j].assign(ba.b, ba.b + jb.poly->E);
-        w_total += (double)jb.poly->s * (double)jb.T;
+        const double w = (double)jb.poly->s * (double)jb.T;
+        w_total += w;
+        if (w >= kPlainRunWork && jb.poly->G) {
+            img.is_plain[j] = 1;
+            img.plain.push_back({j, jb.poly, jb.T, jb.t0, jb.out});
+        } else {
+            w_queue += w;
+        }
     }
+    // a job in the queue: nonempty and not a plain run
+    auto queued = [&](size_t j) { return jobs[j].T && jobs[j].poly->G && !img.is_plain[j]; };
     const uint64_t R = queue_resident_warps();
-    const double w_target = std::max(w_total / (8.0 * (double)R), 32.0 * 64.0);
+    const double w_target = std::max(w_queue / (8.0 * (double)R), 32.0 * 64.0);
     std::vector<PlanHost> ph(njobs);
     std::vector<std::vector<uint32_t>> cs(njobs), cg(njobs);
     std::vector<int> var(njobs);
@@ -216,7 +226,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
         for (size_t j = 0; j < njobs; ++j) {
             img.leader[j] = j;
             pe_poly *P = jobs[j].poly;
-            if (!jobs[j].T || !P->G || !P->E) continue;
+            if (!queued(j) || !P->E) continue;
             std::vector<uint64_t> key{P->p, P->E};
             key.insert(key.end(), img.betas[j].begin(), img.betas[j].end());
             auto it = cls.emplace(key, j).first;
@@ -227,7 +237,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
     }
     for (size_t j = 0; j < njobs; ++j) {
         pe_poly *P = jobs[j].poly;
-        if (!jobs[j].T || !P->G) continue;
+        if (!queued(j)) continue;
         const Tiles t = batch_tiles(P, jobs[j].T, w_target);
         build_plan_host(P, t, jobs[j].T, ph[j]);
         cs[j] = P->chunks.cs;
@@ -245,7 +255,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
     // Items, ordered by decreasing cost (a slab-point of a K-term chunk costs K).
     std::vector<std::pair<double, uint2>> items;
     for (size_t j = 0; j < njobs; ++j) {
-        if (!jobs[j].T || !jobs[j].poly->G) continue;
+        if (!queued(j)) continue;
         const PlanHost &p = ph[j];
         const double lg = std::log2((double)std::max<uint64_t>(2, jobs[j].t0 + jobs[j].T));
         for (uint32_t q = 0; q < p.Q; ++q) {
@@ -264,7 +274,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
     const size_t cnt0 = S.off;
     const size_t off_head = S.take(256);
     for (size_t j = 0; j < njobs; ++j)
-        if (jobs[j].T && jobs[j].poly->G) o_cnt[j] = S.take(ph[j].counter_bytes());
+        if (queued(j)) o_cnt[j] = S.take(ph[j].counter_bytes());
     const size_t cnt1 = S.off;
     // Scratch offsets follow the uploaded region.
     const size_t up = U.off;
@@ -288,7 +298,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
     for (size_t j = 0; j < njobs; ++j) {
         const pe_job &jb = jobs[j];
         pe_poly *P = jb.poly;
-        if (!jb.T || !P->G) continue;
+        if (!queued(j)) continue;
         put(o_cs[j], cs[j].data(), cs[j].size() * 4);
         put(o_cg[j], cg[j].data(), cg[j].size() * 4);
         put(o_unit[j], ph[j].unit.data(), ph[j].unit.size() * 4);
@@ -349,6 +359,15 @@ cudaError_t batch_enqueue(const BatchImage &img, cudaStream_t st)
     cudaError_t e = cudaMemcpyAsync(img.base, img.host.data(), img.host.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     return batch_kernels(img, st);
+}
+
+pe_status batch_run_plain(const BatchImage &img, cudaStream_t st)
+{
+    for (const BatchImage::PlainRun &r : img.plain) {
+        const pe_status s = run_matrix(r.poly, img.betas[r.j].data(), r.T, r.t0, r.out, st);
+        if (s != PE_OK) return s;
+    }
+    return PE_OK;
 }
 
 }  // namespace pe
@@ -415,6 +434,23 @@ extern "C" pe_status poly_eval_batch_launch(pe_batch *B, void *stream)
     }
     cudaError_t e = cudaGraphLaunch(B->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    return batch_run_plain(B->img, (cudaStream_t)stream);
+}
+
+extern "C" pe_status poly_eval_batch_launches(const pe_batch *B, uint32_t *kernels, uint32_t *plain_jobs)
+{
+    if (!B) {
+        set_error("NULL batch");
+        return PE_ERR_ARG;
+    }
+    const BatchImage &I = B->img;
+    uint32_t n = (I.max_entries && I.njobs ? 1u : 0u) + (I.nitems ? 1u : 0u);
+    for (const BatchImage::PlainRun &r : I.plain) {
+        uint32_t k = 0;
+        if (poly_eval_launches_per_run(r.poly, r.T, &k) == PE_OK) n += k;
+    }
+    if (kernels) *kernels = n;
+    if (plain_jobs) *plain_jobs = (uint32_t)I.plain.size();
     return PE_OK;
 }
 
@@ -431,6 +467,7 @@ extern "C" pe_status poly_eval_batch_set_beta(pe_batch *B, size_t j, const uint6
     if (!E) return PE_OK;
     BatchImage &I = B->img;
     I.betas[j].assign(ba.b, ba.b + E);
+    if (I.is_plain[j]) return PE_OK;   // a plain run reads its point from the host at launch
     cudaError_t e = cudaMemcpy(I.base + I.beta_off[j], I.betas[j].data(), E * 8, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "beta upload");
     if (!B->jobs[j].T || !B->jobs[j].poly->G) return PE_OK;

@@ -142,10 +142,26 @@ struct BatchImage {
     uint32_t nitems = 0, njobs = 0, max_entries = 0;
     int grid = 0;
     double term_points = 0.0;
+    // Jobs large enough to fill the GPU on their own take no part in the image:
+    // they run as plain runs (precomputed starting values, their own tiles)
+    // after the queue kernel, on the same stream.
+    struct PlainRun {
+        size_t j;
+        pe_poly *poly;
+        uint64_t T, t0;
+        uint64_t *out;
+    };
+    std::vector<uint8_t> is_plain;            // per job
+    std::vector<PlainRun> plain;
 };
+
+// Work (term-points) from which a batch job runs as a plain run.
+constexpr double kPlainRunWork = 268435456.0;   // 2^28
 
 pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImage &img);
 cudaError_t batch_enqueue(const BatchImage &img, cudaStream_t st);
+// The plain runs of a batch (after batch_enqueue or the batch's graph).
+pe_status batch_run_plain(const BatchImage &img, cudaStream_t st);
 
 }  // namespace pe
 

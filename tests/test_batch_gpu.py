@@ -1,5 +1,7 @@
 """Batched evaluation (one persistent kernel, device work queue, CUDA graph)
 is bit-exact against the oracle and against the plain path (GPU)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -156,6 +158,39 @@ def test_shared_power_tables_and_splitting_them():
     ws[0].beta = rng.integers(2, p, size=4, dtype=np.uint64)
     batch.set_beta(0, ws[0].beta)                        # the leader leaves; job 1 leads alone
     check()
+    batch.close()
+    for q in polys:
+        q.close()
+
+
+def test_jobs_that_fill_the_gpu_run_as_plain_runs():
+    """A job of at least 2^28 term-points leaves the queue for a plain run
+    after the graph; small jobs stay in the queue; both kinds, with new
+    points set between launches, match the oracle."""
+    big = wl.make_zipf(n=7, s=270_000, p=wl.random_prime(62, 91), deg12=20, deg_rest=8, T=1024, seed=92)
+    assert big.s * big.T >= 1 << 28
+    big50 = wl.make_zipf(n=6, s=135_000, p=wl.random_prime(50, 93), deg12=12, deg_rest=6, T=2048, seed=94,
+                         t0=5)
+    ws = [big, big50] + _mixed(6, 95)
+    polys = [pe.Poly.from_workload(w, variant="fp64" if k == 1 else "auto") for k, w in enumerate(ws)]
+    outs = [torch.full((w.T, q.G), -1, dtype=torch.int64, device="cuda") for w, q in zip(ws, polys)]
+    batch = pe.Batch([(q, w.beta, w.T, w.t0, o) for w, q, o in zip(ws, polys, outs)])
+    info = batch.launches()
+    assert info["plain_jobs"] == 2
+    assert info["kernels"] == 2 + 3 + 3                 # power tables + queue; three per plain run
+    for rep in range(2):
+        if rep == 1:                                    # new points for a plain and a queued job
+            for k in (0, 3):
+                ws[k] = dataclasses.replace(ws[k], beta=wl._uniform_mod(np.random.default_rng(k), ws[k].p,
+                                                                          ws[k].n - 2, lo=2))
+                batch.set_beta(k, ws[k].beta)
+        for o in outs:
+            o.fill_(-1)
+        batch.launch()
+        torch.cuda.synchronize()
+        for k, (w, o) in enumerate(zip(ws, outs)):
+            ref = oracle.eval_matrix(w)[1] if k < 2 else oracle.eval_direct(w)[1]
+            assert np.array_equal(pe.to_u64(o), ref), f"launch {rep}, job {k}"
     batch.close()
     for q in polys:
         q.close()
