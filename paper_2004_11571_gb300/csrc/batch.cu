@@ -172,7 +172,7 @@ struct Layout {
 // Plans every job, lays the plans, power tables, scratch and the ordered work
 // queue out in `arena` (grown only when too small) and fills `img.host` with
 // the bytes to upload there.
-pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImage &img)
+pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImage &img, bool plain_runs)
 {
     img = BatchImage{};
     if (njobs && !jobs) {
@@ -195,7 +195,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
         img.betas[j].assign(ba.b, ba.b + jb.poly->E);
         const double w = (double)jb.poly->s * (double)jb.T;
         w_total += w;
-        if (w >= kPlainRunWork && jb.poly->G) {
+        if (plain_runs && w >= kPlainRunWork && jb.poly->G) {
             img.is_plain[j] = 1;
             img.plain.push_back({j, jb.poly, jb.T, jb.t0, jb.out});
         } else {

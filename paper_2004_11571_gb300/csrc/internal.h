@@ -158,7 +158,9 @@ struct BatchImage {
 // Work (term-points) from which a batch job runs as a plain run.
 constexpr double kPlainRunWork = 268435456.0;   // 2^28
 
-pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImage &img);
+// plain_runs = false keeps every job in the queue (server epochs, which overlap
+// on several streams and mix large requests with small ones).
+pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImage &img, bool plain_runs = true);
 cudaError_t batch_enqueue(const BatchImage &img, cudaStream_t st);
 // The plain runs of a batch (after batch_enqueue or the batch's graph).
 pe_status batch_run_plain(const BatchImage &img, cudaStream_t st);

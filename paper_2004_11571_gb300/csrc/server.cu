@@ -291,11 +291,10 @@ struct pe_server {
             jobs[j].out = (uint64_t *)(s.outs.as<unsigned char>() + r->out_off);
             s.term_points += (double)r->poly->s * (double)r->T;
         }
-        pe_status st = batch_build(jobs.data(), jobs.size(), s.arena, s.img);
+        pe_status st = batch_build(jobs.data(), jobs.size(), s.arena, s.img, false);
         t_plan += since(t_pl0);
         const Clock::time_point t_la0 = Clock::now();
         if (st == PE_OK && (e = batch_enqueue(s.img, s.st)) != cudaSuccess) st = cuda_fail(e, "server epoch");
-        if (st == PE_OK) st = batch_run_plain(s.img, s.st);   // requests large enough to fill the GPU alone
         for (size_t j = 0; st == PE_OK && j < ok.size(); ++j) {
             SrvRequest *r = ok[j];
             if (!r->out_bytes) continue;
