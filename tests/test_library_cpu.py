@@ -101,3 +101,10 @@ def test_points_must_fit_in_64_bits(L):
     assert na(p, 1, 1, dummy, dummy, dummy, 0, top, dummy, None) == 0         # no points: nothing to do
     assert na(p, 1 << 31, 1 << 31, dummy, dummy, dummy, 1 << 31, 1, dummy, None) == 1   # 2^62 output values
     assert b"2^60" in L.poly_eval_last_error()
+
+
+def test_batch_queries_validate_their_handle(L):
+    k, n = ctypes.c_uint32(7), ctypes.c_uint32(7)
+    assert L.poly_eval_batch_launches(None, ctypes.byref(k), ctypes.byref(n)) == 1
+    assert b"NULL batch" in L.poly_eval_last_error()
+    assert L.poly_eval_batch_launch(None, None) == 1
