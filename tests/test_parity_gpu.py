@@ -220,6 +220,9 @@ def test_full_size_configs_sampled(name):
         assert int(got.max()) < w.p
         outs.append(got)
     assert np.array_equal(outs[0], outs[1])            # variants agree everywhere
+    if name == "large":                                # the item shape the benchmark's tuner picks and times
+        _, timed = _gpu(w, "barrett64", dict(K=16, slabs=1, tchunk=224, warps_per_block=4, tail=128))
+        assert np.array_equal(timed, outs[0])
     rows, cols = _sample_cells(w, cells.G, 48, 1)
     want = cells(rows + w.t0, cols)
     assert np.array_equal(outs[0][rows, cols], want)
