@@ -13,8 +13,8 @@ The metric is term-point evaluations per second (s*T per step).
   roofline Step B, timed live with events on its stream, against the integer
            multiply issue rate of the SMs at the sampled SM clock
   cpu_baseline  the oracle's Algorithm 1 (single thread) over the workload; also
-           the oracle's plain definition on 1/64 of the groups and Algorithm 1
-           on every host core
+           the oracle's plain definition on 1/64 of the groups, and both on
+           every host core over the whole workload
 
 --impl reference times the oracle instead (the method's plain CPU statement).
 Under torchrun each rank evaluates its own block of T points (weak scaling,
@@ -194,9 +194,10 @@ def cpu_baseline_direct(w, stride=64):
             "seconds": dt}
 
 
-def _oracle_share(config, rank, nproc, barrier, queue):
-    """Child of cpu_baseline_all_cores: Algorithm 1 of the oracle on the groups
-    g with g % nproc == rank, all T points, timed after a common barrier."""
+def _oracle_share(config, rank, nproc, barrier, queue, definition=False):
+    """Child of cpu_baseline_all_cores: Algorithm 1 of the oracle (or its plain
+    definition) on the groups g with g % nproc == rank, all T points, timed
+    after a common barrier."""
     import oracle
     w = make_workload(config)
     _, tg = oracle.group_keys(w.exps)
@@ -205,18 +206,20 @@ def _oracle_share(config, rank, nproc, barrier, queue):
     oracle.build()
     barrier.wait()
     t = time.perf_counter()
-    oracle.eval_matrix(sub)
+    (oracle.eval_direct if definition else oracle.eval_matrix)(sub)
     queue.put((sub.term_points, time.perf_counter() - t))
 
 
-def cpu_baseline_all_cores(config, nproc=None):
-    """The same oracle as independent processes over disjoint group subsets of
-    the full workload, one per host core (spawned, not forked)."""
+def cpu_baseline_all_cores(config, nproc=None, definition=False):
+    """The same oracle (Algorithm 1, or the plain definition) as independent
+    processes over disjoint group subsets of the full workload, one per host
+    core (spawned, not forked)."""
     import multiprocessing as mp
     nproc = nproc or os.cpu_count() or 1
     ctx = mp.get_context("spawn")
     barrier, queue = ctx.Barrier(nproc), ctx.Queue()
-    procs = [ctx.Process(target=_oracle_share, args=(config, r, nproc, barrier, queue)) for r in range(nproc)]
+    procs = [ctx.Process(target=_oracle_share, args=(config, r, nproc, barrier, queue, definition))
+             for r in range(nproc)]
     for pr in procs:
         pr.start()
     try:
@@ -229,8 +232,10 @@ def cpu_baseline_all_cores(config, nproc=None):
         pr.join()
     tp = sum(r[0] for r in res)
     dt = max(r[1] for r in res)
-    return {"value": tp / dt, "unit": "term-points/s", "cores": nproc, "kind": "oracle",
-            "sample": f"Algorithm 1 of the oracle (gcc -O2) as {nproc} processes over disjoint group subsets "
+    what = "the definition in the oracle" if definition else "Algorithm 1 of the oracle"
+    return {"value": tp / dt, "unit": "term-points/s", "cores": nproc,
+            "kind": "oracle (definition)" if definition else "oracle",
+            "sample": f"{what} (gcc -O2) as {nproc} processes over disjoint group subsets "
                       f"(g mod {nproc}) of the full workload: {tp:.3e} term-points, slowest process {dt:.2f} s",
             "seconds": dt}
 
@@ -650,6 +655,7 @@ def run_ours(args):
         line["cpu_baseline_definition"] = cpu_baseline_direct(w)
         if args.config in ("large", "large30", "tiny"):
             line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.config)
+            line["cpu_baseline_definition_all_cores"] = cpu_baseline_all_cores(args.config, definition=True)
     if world == 1 and not args.no_extras:
         line["sparse_images"] = bench_compact(pe, out, torch)
         line["interpolation"] = bench_interp(pe, torch, mhz)
