@@ -163,6 +163,29 @@ def dist_setup():
     return world, rank, local
 
 
+_HOST_CPU = None
+
+
+def host_cpu():
+    """The host CPU's model name and logical core count (lscpu, else /proc/cpuinfo)."""
+    global _HOST_CPU
+    if _HOST_CPU is None:
+        model = ""
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            model = next((l.split(":", 1)[1].strip() for l in out.splitlines() if l.startswith("Model name")), "")
+        except Exception:
+            pass
+        if not model:
+            try:
+                with open("/proc/cpuinfo") as f:
+                    model = next((l.split(":", 1)[1].strip() for l in f if l.lower().startswith("model name")), "")
+            except Exception:
+                pass
+        _HOST_CPU = {"model": model or "unknown", "logical_cores": os.cpu_count() or 0}
+    return _HOST_CPU
+
+
 def cpu_baseline(w, stride):
     """Oracle Algorithm 1 (one thread) on every `stride`-th group, all T points."""
     import oracle
@@ -175,7 +198,7 @@ def cpu_baseline(w, stride):
     return {"value": sub.term_points / dt, "unit": "term-points/s", "cores": 1, "kind": "oracle",
             "sample": f"Algorithm 1 of the oracle (gcc -O2, unsigned __int128) on every {stride}-th group: "
                       f"{sub.s} terms x {w.T} points = {sub.term_points:.3e} term-points in {dt:.1f} s",
-            "seconds": dt}
+            "seconds": dt, "host": host_cpu()}
 
 
 def cpu_baseline_direct(w, stride=64):
@@ -191,7 +214,7 @@ def cpu_baseline_direct(w, stride=64):
     return {"value": sub.term_points / dt, "unit": "term-points/s", "cores": 1, "kind": "oracle (definition)",
             "sample": f"the definition in the oracle (gcc -O2, unsigned __int128) on every {stride}-th group: "
                       f"{sub.s} terms x {w.T} points = {sub.term_points:.3e} term-points in {dt:.1f} s",
-            "seconds": dt}
+            "seconds": dt, "host": host_cpu()}
 
 
 def _oracle_share(config, rank, nproc, barrier, queue, definition=False):
@@ -237,7 +260,7 @@ def cpu_baseline_all_cores(config, nproc=None, definition=False):
             "kind": "oracle (definition)" if definition else "oracle",
             "sample": f"{what} (gcc -O2) as {nproc} processes over disjoint group subsets "
                       f"(g mod {nproc}) of the full workload: {tp:.3e} term-points, slowest process {dt:.2f} s",
-            "seconds": dt}
+            "seconds": dt, "host": host_cpu()}
 
 
 def hbm_peak_gbs():
@@ -502,7 +525,7 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": workload_config(w, args.config, "oracle"),
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": value,
-                             "unit": "term-points/s"},
+                             "unit": "term-points/s", "host": host_cpu()},
             "e2e": {"value": value, "unit": "term-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

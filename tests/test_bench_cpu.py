@@ -20,6 +20,7 @@ def test_reference_arm_prints_one_json_line():
     assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1 and d["vs_baseline"] is None
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["host"]["model"] and d["cpu_baseline"]["host"]["logical_cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["terms"] == 2000 and d["config"]["T"] == 64
 
