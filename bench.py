@@ -12,7 +12,7 @@ The metric is term-point evaluations per second (s*T per step).
            host arrays (upload), run into pinned host memory (download), destroy
   roofline Step B, timed live with events on its stream, against the integer
            multiply issue rate of the SMs at the sampled SM clock
-  cpu_baseline  the oracle's Algorithm 1 (single thread) over the workload; also
+  cpu_baseline  the oracle's matrix method (single thread) over the workload; also
            the oracle's plain definition on 1/64 of the groups, and both on
            every host core over the whole workload
 
@@ -45,7 +45,35 @@ import workloads as wl  # noqa: E402
 # sampled clock and `achieved` is Step B's term-points/s times the weighted count.
 OPS_PER_TP = {"barrett64": {"wide": 3, "hi": 2, "lo": 4}, "mont64": {"wide": 8, "hi": 2, "lo": 4},
               "barrett32": {"wide": 0, "hi": 1, "lo": 2}}
-NUM_SMS = 152
+# FP64-pipe operations per term-point of the FP64 path, counted in the source:
+# Algorithm 2's product (mul, fma, mul, floor, fma, add, and two compare-and-
+# correct pairs: 10) and Algorithm 3's sum (add, compare, correct: 3).
+FP64_OPS_PER_TP = 13
+GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize_images.json")
+_GOLD = None
+
+
+def golden() -> dict:
+    """Stored SHA-256 digests of the oracle's images of the full-size workloads
+    (written by tests/golden/make_fullsize_digests.py; read here as data)."""
+    global _GOLD
+    if _GOLD is None:
+        try:
+            with open(GOLDEN) as f:
+                _GOLD = json.load(f)
+        except Exception:
+            _GOLD = {}
+    return _GOLD
+
+
+def oracle_match(rec, w, out):
+    """True / False when a stored oracle digest exists for exactly these inputs,
+    None otherwise.  `out` is a (T, G) tensor or array of the images."""
+    if not rec or rec.get("inputs") != wl.inputs_digest(w):
+        return None
+    if hasattr(out, "cpu"):
+        out = out.cpu().numpy()
+    return wl.images_digest(out) == rec["images"]
 # DRAM bytes (read + write) of one Step B launch on the large workload, from one
 # ncu capture of the current kernel with the item shape it ran; reported only
 # when the timed plan has that same shape (None for other workloads).
@@ -76,7 +104,8 @@ def parse():
     ap.add_argument("--method", default="auto", choices=["auto", "matrix", "fast"],
                     help="auto: what poly_eval_run picks (the tuner's choice); fast: poly_eval_run_fast")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
-    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="Poisson request rate; 0 = 0.7x the burst capacity measured in the same run")
     ap.add_argument("--serve-burst", type=int, default=1500)
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
     ap.add_argument("--no-tune", action="store_true", help="skip poly_eval_tune before timing")
@@ -187,7 +216,7 @@ def host_cpu():
 
 
 def cpu_baseline(w, stride):
-    """Oracle Algorithm 1 (one thread) on every `stride`-th group, all T points."""
+    """The oracle's matrix method (one thread) on every `stride`-th group, all T points."""
     import oracle
     keys, tg = oracle.group_keys(w.exps)
     sel = (tg % stride) == 0
@@ -196,7 +225,7 @@ def cpu_baseline(w, stride):
     oracle.eval_matrix(sub)
     dt = time.perf_counter() - t
     return {"value": sub.term_points / dt, "unit": "term-points/s", "cores": 1, "kind": "oracle",
-            "sample": f"Algorithm 1 of the oracle (gcc -O2, unsigned __int128) on every {stride}-th group: "
+            "sample": f"the oracle's matrix method (gcc -O2, unsigned __int128) on every {stride}-th group: "
                       f"{sub.s} terms x {w.T} points = {sub.term_points:.3e} term-points in {dt:.1f} s",
             "seconds": dt, "host": host_cpu()}
 
@@ -218,7 +247,7 @@ def cpu_baseline_direct(w, stride=64):
 
 
 def _oracle_share(config, rank, nproc, barrier, queue, definition=False):
-    """Child of cpu_baseline_all_cores: Algorithm 1 of the oracle (or its plain
+    """Child of cpu_baseline_all_cores: the oracle's matrix method (or its plain
     definition) on the groups g with g % nproc == rank, all T points, timed
     after a common barrier."""
     import oracle
@@ -234,7 +263,7 @@ def _oracle_share(config, rank, nproc, barrier, queue, definition=False):
 
 
 def cpu_baseline_all_cores(config, nproc=None, definition=False):
-    """The same oracle (Algorithm 1, or the plain definition) as independent
+    """The same oracle (matrix method, or the plain definition) as independent
     processes over disjoint group subsets of the full workload, one per host
     core (spawned, not forked)."""
     import multiprocessing as mp
@@ -255,7 +284,7 @@ def cpu_baseline_all_cores(config, nproc=None, definition=False):
         pr.join()
     tp = sum(r[0] for r in res)
     dt = max(r[1] for r in res)
-    what = "the definition in the oracle" if definition else "Algorithm 1 of the oracle"
+    what = "the definition in the oracle" if definition else "the oracle's matrix method"
     return {"value": tp / dt, "unit": "term-points/s", "cores": nproc,
             "kind": "oracle (definition)" if definition else "oracle",
             "sample": f"{what} (gcc -O2) as {nproc} processes over disjoint group subsets "
@@ -394,7 +423,7 @@ def bench_fast(pe, torch, mhz, reps=3):
     rates = pe.int_pipe_rates()
     wide, hi = rates["mad_lo"] / rates["mad_wide"], rates["mad_lo"] / rates["mad_hi"]
     shoup_slots, mont_slots = 3 * wide + 2 * hi + 4, 8 * wide + 2 * hi + 4   # lazy Shoup product; Montgomery
-    peak = NUM_SMS * rates["mad_lo"] * mhz * 1e6
+    peak = pe.num_sms() * rates["mad_lo"] * mhz * 1e6
     res = []
     cases = [wl.config_width(62, ntt=True), wl.config_width(62, ntt=True, T=1024),
              wl.make_zipf(n=9, s=1_000_000, p=wl.random_ntt_prime(62, 20, 5), deg12=70, deg_rest=20, T=1024,
@@ -461,7 +490,7 @@ def bench_interp(pe, torch, mhz, reps=10):
     slots_exact = 4 * wide
     slots_b = sum(n * c for n, c in zip(OPS_PER_TP["barrett64"].values(),
                                         (wide, rates["mad_lo"] / rates["mad_hi"], 1.0)))
-    peak = NUM_SMS * rates["mad_lo"] * mhz * 1e6 / 1e9
+    peak = pe.num_sms() * rates["mad_lo"] * mhz * 1e6 / 1e9
     res = []
     for w in (wl.config_interp(), wl.config_interp(seed=wl.SEED_INTERP + 1, s=10_000, u=122, n=9)):
         poly = pe.Poly.from_workload(w)
@@ -501,6 +530,91 @@ def bench_interp(pe, torch, mhz, reps=10):
                     "note": "ms is host-timed per call (tile upload, five or more launches, one synchronization)"})
         poly.close()
         del images, z, c
+    return res
+
+
+def stepb_roofline(pe, vkey, p, s, T, tps_b, stepb_ms, mhz, traffic=None):
+    """Step B against the issue rate of its pipe at the sampled SM clock: the
+    integer multiply pipe (mad.lo slots) for the integer products, the FP64
+    pipe (fma.rn.f64 rate) for Algorithm 2; plus the register-only loop of the
+    same product (poly_eval_modmul_peak) as a second denominator."""
+    sms = pe.num_sms()
+    if vkey == "fp64":
+        rates = pe.fp64_pipe_rates()
+        slots = FP64_OPS_PER_TP
+        peak = sms * rates["fma"] * mhz * 1e6 / 1e9
+        roof = {"bound": "alu", "achieved": tps_b * slots / 1e9, "peak": peak, "unit": "G FP64 op/s",
+                "peak_source": f"{sms} SMs x {rates['fma']:.2f} fma.rn.f64 per SM-clock (measured) x "
+                               f"{mhz:.0f} MHz (median sampled SM clock)",
+                "algorithmic": f"{FP64_OPS_PER_TP} FP64 operations per term-point (Algorithm 2 product 10, "
+                               f"Algorithm 3 sum 3) x {s}x{T} term-points"}
+    else:
+        rates = pe.int_pipe_rates()
+        cost = {"lo": 1.0, "hi": rates["mad_lo"] / rates["mad_hi"], "wide": rates["mad_lo"] / rates["mad_wide"]}
+        slots = sum(n * cost[k] for k, n in OPS_PER_TP[vkey].items())
+        peak = sms * rates["mad_lo"] * mhz * 1e6 / 1e9
+        roof = {"bound": "alu", "achieved": tps_b * slots / 1e9, "peak": peak, "unit": "Gslot/s",
+                "peak_source": f"{sms} SMs x {rates['mad_lo']:.1f} mad.lo.u32 per SM-clock (measured) x "
+                               f"{mhz:.0f} MHz (median sampled SM clock)",
+                "algorithmic": f"{OPS_PER_TP[vkey]} 32-bit multiplies per term-point = {slots:.2f} mad.lo slots "
+                               f"x {s}x{T} term-points"}
+    roof.update({"frac": roof["achieved"] / peak, "traffic": traffic, "kernel": "pe::k_stepB",
+                 "variant": vkey, "sms": sms, "sm_mhz": mhz, "ops_per_term_point": slots,
+                 "peak_term_points_per_s": peak * 1e9 / slots, "stepB_ms": stepb_ms,
+                 "stepB_term_points_per_s": tps_b})
+    try:
+        cal, cal_mhz = pe.modmul_peak(vkey, p)
+        roof.update({"register_only_term_points_per_s": cal, "frac_of_register_only": tps_b / cal,
+                     "register_only_frac_of_peak": cal * slots / (peak * 1e9), "register_only_sm_mhz": cal_mhz})
+    except Exception as ex:  # pragma: no cover
+        roof["register_only_error"] = str(ex)
+    return roof
+
+
+def bench_config(pe, torch, name, w, variant, steps=4, warmup=2, method="matrix", tune=False):
+    """One full-size workload on one product: device time per run (terms
+    resident, L2 flushed between runs), Step B's roofline, and whether the
+    output equals the oracle's stored images."""
+    poly = pe.Poly.from_workload(w, variant=variant)
+    T = int(w.T)
+    if tune and variant == "auto":
+        pe.tune(poly, T)
+    out = torch.empty((T, poly.G), dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    run = poly.run_fast if method == "fast" else poly.run
+    for _ in range(warmup):
+        run(w.beta, T, w.t0, out=out, stream=stream)
+    torch.cuda.synchronize()
+    identical = oracle_match(golden().get("single", {}).get(name), w, out)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    poly.set_timing(True)
+    poly.kernel_times()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        run(w.beta, T, w.t0, out=out, stream=stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    poly.set_timing(False)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    _, t_a, t_b, runs = poly.kernel_times()
+    plan = poly.plan_info(T)
+    vkey = variant if variant in OPS_PER_TP or variant == "fp64" else (
+        "barrett32" if int(w.p) < (1 << 30) else "barrett64")
+    res = {"workload": w.name, "variant": vkey if method == "matrix" else "fast method", "ms_per_run": ms,
+           "term_points_per_s": w.s * T / (ms * 1e-3), "identical_to_oracle": identical,
+           "tiles": {k: plan[k] for k in ("K", "slabs", "tchunk", "warps_per_block", "tail_points", "method")},
+           "clocks": clk}
+    if method == "matrix" and runs and t_b > 0:
+        res["stepA_ms"] = t_a / runs
+        res["roofline"] = stepb_roofline(pe, vkey, int(w.p), w.s, T, w.s * T / (t_b / runs * 1e-3), t_b / runs,
+                                         clk["sm_mhz"] or 1920.0)
+    poly.close()
+    del out, flush
     return res
 
 
@@ -617,10 +731,12 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
-    # Roofline of Step B: integer-multiply issue rate at the sampled SM clock.
-    vkey = variant if variant in OPS_PER_TP else ("barrett32" if int(w.p) < (1 << 30) else "barrett64")
+    # Roofline of Step B: integer-multiply (or FP64) issue rate at the sampled SM clock.
+    vkey = variant if variant in OPS_PER_TP or variant == "fp64" else (
+        "barrett32" if int(w.p) < (1 << 30) else "barrett64")
     tps_b = s * T / (t_b / runs * 1e-3) if runs and t_b > 0 else None
     mhz = clk["sm_mhz"] or 1920.0
+    sms = pe.num_sms()
     roof = None
     if fast_off is not None:
         rates = pe.int_pipe_rates()
@@ -628,38 +744,16 @@ def run_ours(args):
         sh, mo = _fast_counts(fast_off, T)
         slots = sh * (3 * wide + 2 * hi + 4) + mo * (8 * wide + 2 * hi + 4)
         step_s = statistics.mean(step_ms) * 1e-3
-        peak = NUM_SMS * rates["mad_lo"] * mhz * 1e6 / 1e9
+        peak = sms * rates["mad_lo"] * mhz * 1e6 / 1e9
         roof = {"bound": "alu", "achieved": slots / step_s / 1e9, "peak": peak, "unit": "Gslot/s",
                 "frac": slots / step_s / 1e9 / peak, "traffic": None, "kernel": "fast method (all kernels)",
                 "algorithmic": f"{sh} Shoup and {mo} Montgomery products per run (NTT butterflies, scalings, "
                                f"pointwise products), counted from the block structure",
-                "peak_source": f"{NUM_SMS} SMs x {rates['mad_lo']:.1f} mad.lo.u32 per SM-clock (measured) x "
+                "peak_source": f"{sms} SMs x {rates['mad_lo']:.1f} mad.lo.u32 per SM-clock (measured) x "
                                f"{mhz:.0f} MHz (median sampled SM clock)"}
-    elif variant != "fp64" and tps_b:
-        rates = pe.int_pipe_rates()
-        cost = {"lo": 1.0, "hi": rates["mad_lo"] / rates["mad_hi"], "wide": rates["mad_lo"] / rates["mad_wide"]}
-        slots = sum(n * cost[k] for k, n in OPS_PER_TP[vkey].items())
-        peak = NUM_SMS * rates["mad_lo"] * mhz * 1e6 / 1e9
-        ach = tps_b * slots / 1e9
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gslot/s", "frac": ach / peak,
-                "traffic": stepb_traffic(args.config, vkey, plan),
-                "kernel": "pe::k_stepB",
-                "peak_source": f"{NUM_SMS} SMs x {rates['mad_lo']:.1f} mad.lo.u32 per SM-clock (measured) x "
-                               f"{mhz:.0f} MHz (median sampled SM clock)",
-                "algorithmic": f"{OPS_PER_TP[vkey]} 32-bit operations per term-point = {slots:.2f} mad.lo slots "
-                               f"(measured per-SM-clock rates {rates}) x {s}x{T} term-points",
-                "peak_term_points_per_s": peak * 1e9 / slots,
-                "stepB_ms": t_b / runs, "stepB_term_points_per_s": tps_b}
-        try:
-            cal, cal_mhz = pe.modmul_peak(vkey, w.p)
-            roof["calibration"] = {"register_only_term_points_per_s": cal, "frac_of_register_only": tps_b / cal,
-                                   "register_only_frac_of_peak": cal * slots / (peak * 1e9),
-                                   "sm_mhz_in_kernel": cal_mhz}
-        except Exception as ex:  # pragma: no cover
-            roof["calibration"] = {"error": str(ex)}
     elif tps_b:
-        roof = {"bound": "alu", "achieved": tps_b / 1e9, "peak": None, "unit": "Gtp/s", "frac": None,
-                "traffic": None, "kernel": "pe::k_stepB", "stepB_ms": t_b / runs}
+        roof = stepb_roofline(pe, vkey, int(w.p), s, T, tps_b, t_b / runs, mhz,
+                              stepb_traffic(args.config, vkey, plan))
     line = {"metric": "term-point evaluations/s", "value": value, "unit": "term-points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
@@ -672,7 +766,9 @@ def run_ours(args):
             "gpu_launches": launches,
             "kernel_ms_per_step": {"power_tables": t_pt / max(runs, 1), "stepA": t_a / max(runs, 1),
                                    "stepB": t_b / max(runs, 1)},
-            "roofline": roof}
+            "roofline": roof,
+            "identical_to_oracle": oracle_match(golden().get("single", {}).get(args.config), w, out)
+            if t0 == w.t0 and args.method != "fast" else None}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_stride)
         line["cpu_baseline_definition"] = cpu_baseline_direct(w)
@@ -686,6 +782,16 @@ def run_ours(args):
             line["multi_prime"] = bench_multiprime(pe, torch, w)
             line["fast_method"] = bench_fast(pe, torch, mhz)
     poly.close()
+    if world == 1 and not args.no_extras and args.config == "large":
+        # The large workload on the Montgomery product, and the width pair
+        # (4e6 terms, 81 groups, T = 4096): 62-bit on the integer products,
+        # 50-bit on Algorithm 2's FP64 product.
+        line["large_montgomery"] = bench_config(pe, torch, "large", w, "mont64", steps=5, warmup=2)
+        w62, w50 = wl.config_width(62), wl.config_width(50)
+        line["width"] = [bench_config(pe, torch, "width62", w62, "auto", steps=4, warmup=2, tune=True),
+                         bench_config(pe, torch, "width62", w62, "mont64", steps=3, warmup=1),
+                         bench_config(pe, torch, "width50", w50, "fp64", steps=3, warmup=1)]
+        del w62, w50
     if world == 1 and not args.no_extras:
         del out, flush
         torch.cuda.empty_cache()
@@ -700,7 +806,10 @@ def run_ours(args):
 
 def run_batched(args, print_line=True):
     """Config of 512 independent polynomials: one CUDA-graph launch of the
-    persistent kernel vs a loop of per-polynomial poly_eval_run calls."""
+    persistent kernel vs a loop of per-polynomial poly_eval_run calls; the same
+    for the jobs below 2^28 term-points alone (the ones the queue kernel runs:
+    larger jobs leave the graph as plain runs); both outputs checked against the
+    oracle's stored images."""
     import torch
     import paper_2004_11571_gb300 as pe
 
@@ -716,9 +825,12 @@ def run_batched(args, print_line=True):
     from paper_2004_11571_gb300 import sharding
     t0s = [sharding.weak_block(int(w.T), 1, rank)[0] for w in ws]
     tp = sum(w.s * w.T for w in ws)
+    small = [k for k, w in enumerate(ws) if w.s * w.T < (1 << 28)]
+    tp_small = sum(ws[k].s * ws[k].T for k in small)
     t_plan = time.perf_counter()
     batch = pe.Batch([(p, w.beta, w.T, t0, o) for p, w, t0, o in zip(polys, ws, t0s, outs)])
     t_plan = time.perf_counter() - t_plan
+    batch_small = pe.Batch([(polys[k], ws[k].beta, ws[k].T, t0s[k], outs[k]) for k in small])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -733,24 +845,50 @@ def run_batched(args, print_line=True):
         torch.cuda.synchronize()
         return [a.elapsed_time(b2) for a, b2 in evs]
 
-    def loop():
-        for p, w, t0, o in zip(polys, ws, t0s, outs):
-            p.run(w.beta, w.T, t0, out=o, stream=stream)
+    def loop(jobs):
+        for k in jobs:
+            polys[k].run(ws[k].beta, ws[k].T, t0s[k], out=outs[k], stream=stream)
 
+    records = golden().get("batched", {}).get("jobs", [])
+
+    def check():
+        """Jobs whose output equals the oracle's stored images (None: no record for these inputs)."""
+        if rank != 0 or len(records) != len(ws) or any(t0 != w.t0 for t0, w in zip(t0s, ws)):
+            return None
+        torch.cuda.synchronize()
+        res = [oracle_match(r, w, o) for r, w, o in zip(records, ws, outs)]
+        if any(x is None for x in res):
+            return {"identical": None, "jobs_without_record": sum(x is None for x in res)}
+        return {"identical": all(res), "jobs_checked": len(res), "jobs_differing": sum(not x for x in res)}
+
+    every = list(range(len(ws)))
     for _ in range(max(args.warmup, 0)):
         batch.launch(stream)
-        loop()
+        loop(every)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     ms_batch = timed(lambda: batch.launch(stream), args.steps)
-    ms_loop = timed(loop, max(1, args.steps // 2))
     clk = clocks.stop()
+    check_batch = check()
+    for o in outs:
+        o.fill_(-1)
+    ms_loop = timed(lambda: loop(every), max(1, args.steps // 2))
+    check_loop = check()
+    for _ in range(2):
+        batch_small.launch(stream)
+        loop(small)
+    ms_small_batch = timed(lambda: batch_small.launch(stream), args.steps)
+    ms_small_loop = timed(lambda: loop(small), args.steps)
     v_batch = tp / (statistics.mean(ms_batch) * 1e-3)
     v_loop = tp / (statistics.mean(ms_loop) * 1e-3)
+    v_sb = tp_small / (statistics.mean(ms_small_batch) * 1e-3)
+    v_sl = tp_small / (statistics.mean(ms_small_loop) * 1e-3)
     launches_loop = sum(p.launches_per_run(w.T) for p, w in zip(polys, ws))
     bl = batch.launches()
+    bls = batch_small.launches()
     batch.close()
+    batch_small.close()
     for p in polys:
         p.close()
     if rank != 0:
@@ -760,7 +898,14 @@ def run_batched(args, print_line=True):
                "term_points": tp, "batched_term_points_per_s": v_batch, "ms_per_launch": statistics.mean(ms_batch),
                "plain_loop_term_points_per_s": v_loop, "plain_loop_ms": statistics.mean(ms_loop),
                "batched_over_plain_loop": v_batch / v_loop, "launches_batched": bl["kernels"],
-               "plain_run_jobs": bl["plain_jobs"], "launches_plain_loop": launches_loop}
+               "plain_run_jobs": bl["plain_jobs"], "launches_plain_loop": launches_loop,
+               "oracle_check_batched": check_batch, "oracle_check_plain_loop": check_loop,
+               "queue_jobs": {"jobs": len(small), "term_points": tp_small,
+                              "batched_term_points_per_s": v_sb, "ms_per_launch": statistics.mean(ms_small_batch),
+                              "plain_loop_term_points_per_s": v_sl, "plain_loop_ms": statistics.mean(ms_small_loop),
+                              "batched_over_plain_loop": v_sb / v_sl, "launches_batched": bls["kernels"],
+                              "note": "the jobs below 2^28 term-points, which the queue kernel runs"},
+               "clocks": clk}
     if not print_line:
         return summary
     line = {"metric": "term-point evaluations/s (batched)", "value": v_batch * world, "unit": "term-points/s",
@@ -773,6 +918,8 @@ def run_batched(args, print_line=True):
             "clocks": clk, "plain_loop": {"value": v_loop, "ms_per_step": statistics.mean(ms_loop),
                                           "launches": launches_loop},
             "batched_over_plain_loop": v_batch / v_loop, "gpu_launches": bl["kernels"] * args.steps,
+            "queue_jobs": summary["queue_jobs"], "oracle_check_batched": check_batch,
+            "oracle_check_plain_loop": check_loop,
             "host_seconds": {"generate": t_gen, "create": t_create, "plan_and_capture": t_plan}}
     print(json.dumps(line), flush=True)
     return summary
@@ -822,7 +969,9 @@ def run_served(args, pool=None):
     resident polynomial at a new beta).  Three measurements: a burst submitted
     back to back (throughput at saturation), the same requests through the plain
     path one by one (create, run into host memory, destroy), and a Poisson
-    stream at the configured rate (latency)."""
+    stream at 0.7x the burst's request rate (or --serve-rate) for latency below
+    saturation.  Requests in the stored seeded sample (~1%) are compared with
+    the oracle's images."""
     import torch
     import paper_2004_11571_gb300 as pe
 
@@ -831,19 +980,30 @@ def run_served(args, pool=None):
         pool = wl.config_batched(seed=wl.SEED_SERVE, count=args.batch_count)
     G = [int(len(np.unique(w.exps[:, 0].astype(np.int64) * 65536 + w.exps[:, 1]))) for w in pool]
     ring = PinnedRing(6 << 30)
+    sample = {r["index"]: r for r in golden().get("served", {}).get("sample", [])}
+    if args.batch_count != 512:
+        sample = {}
 
     submit_s = [0.0]
 
     def drive(reqs, srv, paced):
-        ids, inflight = {}, []
+        ids = {}
         start = time.perf_counter()
         tp = 0.0
+        checks = {"checked": 0, "matched": 0, "without_record": 0}
 
         def wait_oldest():
-            s0, e0, t = ring.regions.pop(0)
+            s0, e0, (t, i, shape) = ring.regions.pop(0)
             srv.poll(t)
+            if i in sample:
+                ok = oracle_match(sample[i], wl.served_workload(pool, reqs[i]), ring.view(s0, shape))
+                if ok is None:
+                    checks["without_record"] += 1
+                else:
+                    checks["checked"] += 1
+                    checks["matched"] += int(ok)
 
-        for (ts, k, beta) in reqs:
+        for i, (ts, k, beta) in enumerate(reqs):
             w = pool[k]
             if paced:
                 delay = start + ts - time.perf_counter()
@@ -872,20 +1032,21 @@ def run_served(args, pool=None):
                     else:
                         time.sleep(0.001)
             submit_s[0] += time.perf_counter() - ts0
-            ring.commit(off, shape[0] * shape[1] * 8, ticket)
+            ring.commit(off, shape[0] * shape[1] * 8, (ticket, i, shape))
             tp += w.s * w.T
         while ring.regions:
             wait_oldest()
-        return time.perf_counter() - start, tp
+        checks["identical"] = (checks["matched"] == checks["checked"]) if checks["checked"] else None
+        return time.perf_counter() - start, tp, checks
 
-    reqs = wl.served_requests(seed=wl.SEED_SERVE, rate=args.serve_rate, duration=args.serve_seconds, pool=pool)
-    burst = reqs[:args.serve_burst]
+    burst = wl.served_requests(seed=wl.SEED_SERVE, rate=2000.0, duration=1.0 + args.serve_burst / 2000.0,
+                               pool=pool)[:args.serve_burst]
     # (1) burst: throughput at saturation
     srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
     drive(burst[:50], srv, False)                      # warm-up
     srv.close()
     srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
-    t_burst, tp_burst = drive(burst, srv, False)
+    t_burst, tp_burst, chk_burst = drive(burst, srv, False)
     st_burst = srv.stats()
     srv.close()
     # (2) the plain path, one request at a time
@@ -904,26 +1065,31 @@ def run_served(args, pool=None):
     t_plain = time.perf_counter() - t0
     for p in polys.values():
         p.close()
-    # (3) Poisson stream at the configured rate
+    # (3) Poisson stream below saturation: 0.7x the burst's request rate unless a rate is given
+    capacity = len(burst) / t_burst
+    rate = args.serve_rate if args.serve_rate > 0 else 0.7 * capacity
+    reqs = wl.served_requests(seed=wl.SEED_SERVE, rate=rate, duration=args.serve_seconds, pool=pool)
     srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
     submit_s[0] = 0.0
-    t_pois, tp_pois = drive(reqs, srv, True)
+    t_pois, tp_pois, chk_pois = drive(reqs, srv, True)
     st_pois = srv.stats()
     srv.close()
     return {
         "workload": f"requests from the {len(pool)}-polynomial batched mixture, 30% reuse a resident "
                     "polynomial at a new beta, 40 GB resident cap",
         "burst": {"requests": len(burst), "seconds": t_burst, "term_points_per_s": tp_burst / t_burst,
-                  "requests_per_s": len(burst) / t_burst, "p50_ms": st_burst["p50_ms"],
-                  "p99_ms": st_burst["p99_ms"], "epochs": st_burst["epochs"], "rejected": st_burst["rejected"]},
+                  "requests_per_s": capacity, "p50_ms": st_burst["p50_ms"],
+                  "p99_ms": st_burst["p99_ms"], "epochs": st_burst["epochs"], "rejected": st_burst["rejected"],
+                  "oracle_check": chk_burst},
         "plain_per_request": {"requests": len(burst), "seconds": t_plain, "term_points_per_s": tp_plain / t_plain,
                               "requests_per_s": len(burst) / t_plain},
         "served_over_plain": (tp_burst / t_burst) / (tp_plain / t_plain),
-        "poisson": {"rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "requests": len(reqs),
+        "poisson": {"rate_per_s": rate, "rate_over_burst_capacity": rate / capacity,
+                    "seconds": args.serve_seconds, "requests": len(reqs),
                     "completed": st_pois["completed"], "achieved_requests_per_s": len(reqs) / t_pois,
                     "goodput_term_points_per_s": tp_pois / t_pois, "p50_ms": st_pois["p50_ms"],
                     "p99_ms": st_pois["p99_ms"], "max_ms": st_pois["max_ms"], "rejected": st_pois["rejected"],
-                    "evictions": st_pois["evictions"], "epochs": st_pois["epochs"],
+                    "evictions": st_pois["evictions"], "epochs": st_pois["epochs"], "oracle_check": chk_pois,
                     "host_seconds": {"client_submit": submit_s[0], "worker_upload": st_pois["upload_s"],
                                      "worker_plan": st_pois["plan_s"], "worker_launch": st_pois["launch_s"],
                                      "worker_finish": st_pois["finish_s"], "gpu_busy": st_pois["busy_s"]}},

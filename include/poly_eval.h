@@ -314,6 +314,9 @@ pe_status poly_eval_vandermonde_timing(int enable, double ms[4]);
  *   m         : device, s monomial values m_i = M_i(beta) in [0, p) (Step A).
  *   group_off : device, G+1 uint32 offsets: group g is terms
  *               group_off[g] .. group_off[g+1]-1 (nonempty, group_off[G] = s).
+ *               The offsets stay on the device and are not checked: offsets
+ *               that break this rule give unspecified images but no access
+ *               outside the inputs, the output or the scratch array.
  *   out       : device, T x G, row r = image at point t0 + r.
  * Asynchronous on `stream`.  The first call on a device looks up the scratch
  * address with that device current; make it before any stream capture.
@@ -324,6 +327,17 @@ pe_status poly_eval_vandermonde_timing(int enable, double ms[4]);
 pe_status poly_eval_stepb_noalloc(uint64_t p, uint64_t s, uint64_t G, const uint64_t *coeffs,
                                   const uint64_t *m, const uint32_t *group_off, uint64_t T, uint64_t t0,
                                   uint64_t *out, void *stream);
+
+/*
+ * The work decomposition poly_eval_stepb_noalloc would use for s terms and T
+ * points, without running anything: shape[0] = work units U (each kslabs
+ * whole slabs of 32 terms), shape[1] = T-chunks Q, shape[2] = points per
+ * T-chunk Tc, shape[3] = kslabs.  Host-only; it reads the device's SM count.
+ * All zero for s = 0 or T = 0.  Errors: PE_ERR_ARG for a NULL shape, sizes
+ * out of range, or inputs too large for the fixed scratch (the same
+ * rejection as poly_eval_stepb_noalloc).  The paper has no counterpart.
+ */
+pe_status poly_eval_stepb_noalloc_shape(uint64_t s, uint64_t T, uint32_t shape[4]);
 
 /* -------------------------------------------------------------------------
  * Batched evaluation: many polynomials, each with its own beta, T, t0 and
@@ -452,6 +466,19 @@ pe_status poly_eval_modmul_peak(pe_variant variant, uint64_t p, double *term_poi
  * rates[3] add.u32.  They are the unit counts behind the integer roofline.
  */
 pe_status poly_eval_int_pipe_rates(double rates[4]);
+
+/*
+ * Measured issue rates of single FP64 instructions, in thread operations per
+ * SM per clock, from independent dependency chains at full occupancy:
+ * rates[0] fma.rn.f64, rates[1] add.rn.f64.  They are the unit counts behind
+ * the roofline of Algorithm 2's product (paper Sect. 3.2), which runs on the
+ * FP64 pipe.
+ */
+pe_status poly_eval_fp64_pipe_rates(double rates[2]);
+
+/* Streaming multiprocessors of the current device (the unit count of every
+ * roofline above).  Errors: PE_ERR_ARG for NULL, PE_ERR_CUDA without a device. */
+pe_status poly_eval_num_sms(uint32_t *sms);
 
 #ifdef __cplusplus
 }

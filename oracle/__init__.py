@@ -5,11 +5,12 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 library: ``oracle.c`` is compiled by gcc into its own shared object, and the
 brute-force evaluator in ``brute.py`` uses exact Python integers.
 
-Functions (paper Sect. 2.3 definition of the bivariate images, Algorithm 1):
+Functions (paper Sect. 2.3: the definition of the bivariate images and the
+matrix method's recurrence):
   group_keys(exps)                -> (keys[G,2], term_group[s])
   eval_direct(w)                  -> (keys, out[T,G])   O1, the definition
   eval_cells(w, t_abs, g)         -> values of chosen cells, O1 per cell
-  eval_matrix(w)                  -> (keys, out[T,G])   O2, Algorithm 1 restated
+  eval_matrix(w)                  -> (keys, out[T,G])   O2, the recurrence M_i(beta^t) = m_i^t
   mulmod / addmod / powmod        -> the scalar F_p operations, for pins
   power_sums(p, z, c, t0, K)      -> a_k = sum_i c_i z_i^(t0+k), k < K
   tvandermonde_solve(p, z, a, t0) -> c with power_sums(p, z, c, t0, n) = a
@@ -148,7 +149,7 @@ def eval_direct(w, T=None, t0=None):
 
 
 def eval_matrix(w, T=None, t0=None):
-    """O2: Algorithm 1 restated (t0 >= 1)."""
+    """O2: the matrix method's recurrence, term by term (t0 >= 1)."""
     T = w.T if T is None else T
     t0 = w.t0 if t0 is None else t0
     coeffs, exps, beta = _arrays(w)

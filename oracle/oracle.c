@@ -22,10 +22,10 @@
  *   oracle_eval_direct : O1, the definition above.  A per-t table of
  *                        (beta_k^t)^e for e <= max degree is the only memo.
  *   oracle_eval_cells  : the same definition for a list of (t, g) cells.
- *   oracle_eval_matrix : O2, Algorithm 1 of the paper restated: m_i = M_i(beta)
- *                        from power tables (Sect. 2.3), then T rounds of
- *                        a_i <- a_i * m_i followed by the coefficient
- *                        reduction over each group.  It is the CPU baseline.
+ *   oracle_eval_matrix : O2, the matrix method's recurrence (Sect. 2.3):
+ *                        m_i = M_i(beta) from power tables, then each term's
+ *                        value at successive points by one product per
+ *                        point, M_i(beta^t) = m_i^t.  It is the CPU baseline.
  *   oracle_power_sums  : the images of one (x1, x2) coefficient with known
  *                        monomial values z_i: a_k = sum_i c_i z_i^(t0+k).
  *   oracle_tvandermonde_solve : the inverse, interpolation from those images
@@ -195,15 +195,18 @@ int oracle_eval_cells(uint64_t p, uint32_t n, uint64_t s, const uint64_t *coeffs
     return 0;
 }
 
-/* ------------------------------------------------- O2: Algorithm 1 ---- */
+/* -------------------------------------------- O2: the matrix method ---- */
 
 /*
- * The matrix method: power tables [beta_k^i, 0 <= i <= d_k] (Sect. 2.3), the
- * monomial values m_i = M_i(beta) with n-3 products each, then for every
- * point a_i <- a_i (x) m_i and c <- c (+) a_i over each run of terms with the
- * same (d_i, e_i) (Algorithm 1).  Terms are visited in group order; the run
- * for group g is the list of its terms.  Requires t0 >= 1: the state before
- * the first point is a_i * m_i^(t0-1).
+ * The matrix method's recurrence (Sect. 2.3): since M_i(beta^t) = m_i^t with
+ * m_i = M_i(beta), the term a_i M_i(beta^t) at point t is the one at point t-1
+ * times m_i.  This evaluator takes the groups one at a time; for each term of
+ * the group it computes m_i from power tables [beta_k^e, 0 <= e <= d_k]
+ * (n-3 products), starts from a_i m_i^(t0-1), and walks the T points with one
+ * product per point, adding each value into the group's row of T sums.  It
+ * does the same sT products and sums as the paper's matrix method, in a
+ * different order (the method itself advances every term by one point before
+ * the next point; order does not matter in F_p).  Requires t0 >= 1.
  */
 int oracle_eval_matrix(uint64_t p, uint32_t n, uint64_t s, const uint64_t *coeffs,
                        const uint32_t *exps, const uint64_t *beta, uint64_t T, uint64_t t0,
@@ -211,49 +214,42 @@ int oracle_eval_matrix(uint64_t p, uint32_t n, uint64_t s, const uint64_t *coeff
 {
     if (p < 2 || n < 2 || t0 < 1) return 1;
     uint32_t E = n - 2;
-    uint64_t *m = (uint64_t *)malloc((s ? s : 1) * sizeof(uint64_t));
-    uint64_t *a = (uint64_t *)malloc((s ? s : 1) * sizeof(uint64_t));
-    uint64_t *order = (uint64_t *)malloc((s ? s : 1) * sizeof(uint64_t));
-    uint64_t *start = (uint64_t *)calloc(G + 1, sizeof(uint64_t));
-    /* group runs (terms of group g are order[start[g] .. start[g+1])) */
-    for (uint64_t i = 0; i < s; ++i) start[term_group[i] + 1]++;
-    for (uint64_t g = 0; g < G; ++g) start[g + 1] += start[g];
-    uint64_t *fill = (uint64_t *)malloc((G + 1) * sizeof(uint64_t));
-    memcpy(fill, start, (G + 1) * sizeof(uint64_t));
-    for (uint64_t i = 0; i < s; ++i) order[fill[term_group[i]]++] = i;
-    free(fill);
-    /* power tables */
+    /* terms of group g: members[first[g] .. first[g+1]) */
+    uint64_t *first = (uint64_t *)calloc(G + 1, sizeof(uint64_t));
+    uint64_t *members = (uint64_t *)malloc((s ? s : 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < s; ++i) first[term_group[i] + 1]++;
+    for (uint64_t g = 0; g < G; ++g) first[g + 1] += first[g];
+    uint64_t *next = (uint64_t *)malloc((G + 1) * sizeof(uint64_t));
+    memcpy(next, first, (G + 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < s; ++i) members[next[term_group[i]]++] = i;
+    free(next);
+    /* power tables: pw[j][e] = beta_j^e for e <= the largest exponent of x_{j+3} */
     uint32_t *deg = (uint32_t *)malloc((E ? E : 1) * sizeof(uint32_t));
-    size_t tab_sz = 0;
-    for (uint32_t j = 0; j < E; ++j) { deg[j] = max_exp(n, s, exps, 2 + j); tab_sz += deg[j] + 1; }
-    uint64_t *tab = (uint64_t *)malloc((tab_sz ? tab_sz : 1) * sizeof(uint64_t));
-    uint64_t **row = (uint64_t **)malloc((E ? E : 1) * sizeof(uint64_t *));
-    size_t off = 0;
-    for (uint32_t j = 0; j < E; ++j) {
-        row[j] = tab + off;
-        row[j][0] = 1 % p;
-        for (uint32_t e = 1; e <= deg[j]; ++e) row[j][e] = oracle_mulmod(row[j][e - 1], beta[j], p);
-        off += deg[j] + 1;
+    size_t cells = 0;
+    for (uint32_t j = 0; j < E; ++j) { deg[j] = max_exp(n, s, exps, 2 + j); cells += deg[j] + 1; }
+    uint64_t *pw = (uint64_t *)malloc((cells ? cells : 1) * sizeof(uint64_t));
+    uint64_t **tab = (uint64_t **)malloc((E ? E : 1) * sizeof(uint64_t *));
+    for (uint32_t j = 0, at = 0; j < E; at += deg[j] + 1, ++j) {
+        tab[j] = pw + at;
+        tab[j][0] = 1 % p;
+        for (uint32_t e = 1; e <= deg[j]; ++e) tab[j][e] = oracle_mulmod(tab[j][e - 1], beta[j], p);
     }
-    /* m_i = M_i(beta) and the starting state a_i * m_i^(t0-1) */
-    for (uint64_t k = 0; k < s; ++k) {
-        uint64_t i = order[k], mi = 1 % p;
-        for (uint32_t j = 0; j < E; ++j) mi = oracle_mulmod(mi, row[j][exps[i * n + 2 + j]], p);
-        m[k] = mi;
-        a[k] = oracle_mulmod(coeffs[i] % p, oracle_powmod(mi, t0 - 1, p), p);
-    }
-    /* Algorithm 1 */
-    for (uint64_t r = 0; r < T; ++r) {
-        for (uint64_t g = 0; g < G; ++g) {
-            uint64_t c = 0;
-            for (uint64_t k = start[g]; k < start[g + 1]; ++k) {
-                a[k] = oracle_mulmod(a[k], m[k], p);
-                c = oracle_addmod(c, a[k], p);
+    uint64_t *sums = (uint64_t *)malloc((T ? T : 1) * sizeof(uint64_t));
+    for (uint64_t g = 0; g < G; ++g) {
+        memset(sums, 0, (T ? T : 1) * sizeof(uint64_t));
+        for (uint64_t q = first[g]; q < first[g + 1]; ++q) {
+            const uint64_t i = members[q];
+            uint64_t m = 1 % p;
+            for (uint32_t j = 0; j < E; ++j) m = oracle_mulmod(m, tab[j][exps[i * n + 2 + j]], p);
+            uint64_t v = oracle_mulmod(coeffs[i] % p, oracle_powmod(m, t0 - 1, p), p);
+            for (uint64_t r = 0; r < T; ++r) {      /* v = a_i m_i^(t0+r) */
+                v = oracle_mulmod(v, m, p);
+                sums[r] = oracle_addmod(sums[r], v, p);
             }
-            out[r * G + g] = c;
         }
+        for (uint64_t r = 0; r < T; ++r) out[r * G + g] = sums[r];
     }
-    free(m); free(a); free(order); free(start); free(deg); free(tab); free(row);
+    free(first); free(members); free(deg); free(pw); free(tab); free(sums);
     return 0;
 }
 

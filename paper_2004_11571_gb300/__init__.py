@@ -139,6 +139,8 @@ def lib():
             "poly_eval_modmul_peak": (st, [ctypes.c_int, _u64, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]),
             "poly_eval_int_pipe_rates": (st, [ctypes.POINTER(ctypes.c_double)]),
+            "poly_eval_fp64_pipe_rates": (st, [ctypes.POINTER(ctypes.c_double)]),
+            "poly_eval_num_sms": (st, [ctypes.POINTER(ctypes.c_uint32)]),
             "poly_eval_compact": (st, [_vp, _u64, _u64, _vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
             "poly_eval_monomials": (st, [_vp, _vp, _vp, _vp, _vp]),
             "poly_eval_create_like": (st, [_vp, _u64, _vp, _u32, ctypes.c_int, ctypes.POINTER(_vp)]),
@@ -147,6 +149,7 @@ def lib():
             "poly_eval_vandermonde_solve": (st, [_u64, _u64, _vp, _vp, _vp, _u64, _u64, _u64, _vp, _vp]),
             "poly_eval_vandermonde_timing": (st, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
             "poly_eval_stepb_noalloc": (st, [_u64, _u64, _u64, _vp, _vp, _vp, _u64, _u64, _vp, _vp]),
+            "poly_eval_stepb_noalloc_shape": (st, [_u64, _u64, ctypes.POINTER(ctypes.c_uint32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -474,6 +477,14 @@ def stepb_noalloc(p: int, coeffs, m, group_off, T: int, t0: int, out, stream=Non
     return out
 
 
+def stepb_noalloc_shape(s: int, T: int) -> dict:
+    """The work decomposition stepb_noalloc uses for s terms and T points
+    (poly_eval_stepb_noalloc_shape): units, T-chunks, points per chunk, slabs per unit."""
+    sh = (ctypes.c_uint32 * 4)()
+    _check(lib().poly_eval_stepb_noalloc_shape(int(s), int(T), sh))
+    return {"units": sh[0], "tchunks": sh[1], "tchunk": sh[2], "kslabs": sh[3]}
+
+
 def modmul_peak(variant="barrett64", p: int = (1 << 61) - 1):
     """(term-points/s, SM MHz) of the register-only Step B inner loop."""
     tps, mhz = ctypes.c_double(), ctypes.c_double()
@@ -533,6 +544,20 @@ def int_pipe_rates() -> dict:
     r = (ctypes.c_double * 4)()
     _check(lib().poly_eval_int_pipe_rates(r))
     return {"mad_lo": r[0], "mad_hi": r[1], "mad_wide": r[2], "add": r[3]}
+
+
+def fp64_pipe_rates() -> dict:
+    """Thread operations per SM per clock of fma.rn.f64 / add.rn.f64."""
+    r = (ctypes.c_double * 2)()
+    _check(lib().poly_eval_fp64_pipe_rates(r))
+    return {"fma": r[0], "add": r[1]}
+
+
+def num_sms() -> int:
+    """Streaming multiprocessors of the current device (poly_eval_num_sms)."""
+    n = ctypes.c_uint32()
+    _check(lib().poly_eval_num_sms(ctypes.byref(n)))
+    return int(n.value)
 
 
 def to_u64(t) -> np.ndarray:

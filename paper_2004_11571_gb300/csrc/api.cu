@@ -778,7 +778,7 @@ extern "C" pe_status poly_eval_debug_fail_alloc(uint32_t nth)
 
 extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out) { return create_poly(d, out, true); }
 
-pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_threads)
+pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_threads, bool allow_device)
 {
     if (!out) {
         set_error("out is NULL");
@@ -813,7 +813,7 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
     }
     pe_status st = check_prime(d->p, variant);
     if (st != PE_OK) return st;
-    if (d->s >= kDeviceCreateMin) {
+    if (allow_device && d->s >= kDeviceCreateMin) {
         bool fallback = false;
         st = create_poly_device(d, variant, out, host_threads, &fallback);
         if (!fallback) return st;

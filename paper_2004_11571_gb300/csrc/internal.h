@@ -243,5 +243,9 @@ pe_status check_beta(const pe_poly *poly, const uint64_t *beta, BetaArg *arg);
 // Frees a polynomial whose device work is known to have completed (no device synchronization).
 void destroy_idle(pe_poly *poly);
 // poly_eval_create with control over host threads (the server parallelizes across uploads instead).
-pe_status create_poly(const pe_poly_desc *desc, pe_poly **out, bool host_threads);
+// host_threads: split host passes over the host pool.  allow_device: inputs of
+// at least 2^14 terms may be checked, grouped and packed by kernels on the
+// device (two synchronizations) instead of on the host; callers whose GPU is
+// held by long kernels (the server) keep the host path, which needs only copies.
+pe_status create_poly(const pe_poly_desc *desc, pe_poly **out, bool host_threads, bool allow_device = true);
 }  // namespace pe

@@ -163,9 +163,90 @@ static pe_status int_rate(double *per_sm_clk)
     return PE_OK;
 }
 
+// FP64 pipe rates: 8 independent dependency chains per thread of fma.rn.f64
+// (x <- x*y + c, y just below 1, so x stays bounded) or add.rn.f64.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_fp64_rate(double *sink, uint32_t iters, unsigned long long *clk)
+{
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 1.0 + (double)((tid * 2654435761u + k * 40503u) & 1023) * 1e-4;
+    const double y = 0.9999995 - (double)(tid & 7) * 1e-9, c = 1e-3 + (double)(tid >> 5 & 15) * 1e-7;
+    unsigned long long c0 = 0, g0 = 0;
+    if (tid == 0) {
+        c0 = clock64();
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g0));
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if constexpr (KIND == 0) asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(x[k]) : "d"(y), "d"(c));
+                if constexpr (KIND == 1) asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(x[k]) : "d"(c));
+            }
+        }
+    }
+    if (tid == 0) {
+        unsigned long long g1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g1));
+        clk[0] = clock64() - c0;
+        clk[1] = g1 - g0;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc += x[k];
+    sink[tid] = acc;
+}
+
+template <int KIND>
+static pe_status fp64_rate(double *per_sm_clk)
+{
+    int bps = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_fp64_rate<KIND>, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    bps = std::max(1, bps);
+    const uint32_t grid = (uint32_t)(bps * num_sms());
+    const uint64_t threads = (uint64_t)grid * 256;
+    DevBuf sink, clk;
+    if ((e = sink.ensure(threads * 8)) != cudaSuccess || (e = clk.ensure(16)) != cudaSuccess)
+        return cuda_fail(e, "alloc");
+    const uint32_t iters = 1u << 10;
+    k_fp64_rate<KIND><<<grid, 256>>>(sink.as<double>(), iters / 16, clk.as<unsigned long long>());  // warm-up
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a);
+    k_fp64_rate<KIND><<<grid, 256>>>(sink.as<double>(), iters, clk.as<unsigned long long>());
+    cudaEventRecord(b);
+    unsigned long long hc[2] = {0, 0};
+    float ms = 0.f;
+    if ((e = cudaEventSynchronize(b)) == cudaSuccess && (e = cudaGetLastError()) == cudaSuccess)
+        e = cudaMemcpy(hc, clk.p, 16, cudaMemcpyDeviceToHost);
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_fail(e, "fp64 rate");
+    const double hz = hc[1] ? (double)hc[0] / (double)hc[1] * 1e9 : 1.9e9;
+    *per_sm_clk = (double)threads * iters * 32.0 / ((double)num_sms() * (ms * 1e-3) * hz);
+    return PE_OK;
+}
+
 }  // namespace pe
 
 using namespace pe;
+
+extern "C" pe_status poly_eval_fp64_pipe_rates(double rates[2])
+{
+    if (!rates) {
+        set_error("NULL output");
+        return PE_ERR_ARG;
+    }
+    pe_status st;
+    if ((st = fp64_rate<0>(&rates[0])) != PE_OK || (st = fp64_rate<1>(&rates[1])) != PE_OK) return st;
+    return PE_OK;
+}
 
 extern "C" pe_status poly_eval_int_pipe_rates(double rates[4])
 {
@@ -200,4 +281,18 @@ extern "C" pe_status poly_eval_modmul_peak(pe_variant variant, uint64_t p, doubl
     case PE_MODMUL_BARRETT64: return run_peak<VAR_BARRETT>(mc, tps, mhz);
     default: set_error("unknown variant"); return PE_ERR_ARG;
     }
+}
+
+extern "C" pe_status poly_eval_num_sms(uint32_t *sms)
+{
+    if (!sms) {
+        set_error("NULL output");
+        return PE_ERR_ARG;
+    }
+    int dev = 0, n = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "SM count");
+    *sms = (uint32_t)n;
+    return PE_OK;
 }

@@ -157,7 +157,12 @@ __global__ void __launch_bounds__(kNaWarps * 32) k_stepB_noalloc(NoAllocJob J)
         const bool has = side == 0 ? lslot >= 0 : rslot >= 0;
         if (!has) continue;
         const uint32_t g = side == 0 ? gL : gR;
-        const uint32_t ua = J.goff[g] / per_unit, ub = (J.goff[g + 1] - 1) / per_unit;
+        // Offsets that break the contract (decreasing, or past s) must not
+        // send the span outside the carry slots and counters: clamp it to the
+        // units that exist.  Such inputs give unspecified images, never a
+        // stray access.
+        const uint32_t ua = min(J.goff[g] / per_unit, J.U - 1);
+        const uint32_t ub = max(ua, min((J.goff[g + 1] - 1) / per_unit, J.U - 1));
         uint32_t last = 0;
         if (lane == 0) last = atomicAdd(&J.counters[(uint64_t)ua * J.Q + q], 1u) + 1u == ub - ua + 1;
         last = __shfl_sync(FULL, last, 0);
@@ -174,6 +179,47 @@ __global__ void __launch_bounds__(kNaWarps * 32) k_stepB_noalloc(NoAllocJob J)
             J.out[row * J.G + g] = reduce96(alo, ahi, mc);
         }
     }
+}
+
+// Work units of kslabs whole 32-term slabs and Q T-chunks of Tc points, with
+// the byte offsets of the carry slots and chain buffers in the scratch array.
+struct NoAllocShape {
+    uint32_t U = 0, Q = 0, Tc = 0, kslabs = 0;
+    size_t off_carry = 0, off_chain = 0, need = 0;
+};
+
+// Tile choice: whole slabs per unit, as few as fit the scratch, and enough
+// T-chunks to give every SM work.  At least one unit per SM (or per slab when
+// there are fewer slabs): a larger kslabs would leave most of the GPU idle, so
+// such inputs are rejected (returns false).
+static bool na_plan(uint64_t s, uint64_t T, NoAllocShape &out)
+{
+    const uint64_t items_target = (uint64_t)num_sms() * 16;
+    const uint64_t slabs = (s + 31) / 32;
+    const uint64_t min_units = std::min<uint64_t>(slabs, (uint64_t)num_sms());
+    for (uint32_t k = 1; k <= (1u << 20); k *= 2) {
+        const uint64_t U = (s + 32ull * k - 1) / (32ull * k);
+        if (U < min_units) break;
+        uint64_t Q = (items_target + U - 1) / U;
+        Q = std::max<uint64_t>(1, std::min<uint64_t>(Q, std::max<uint64_t>(1, T / 32)));
+        const uint64_t Tc = (T + Q - 1) / Q;
+        Q = (T + Tc - 1) / Tc;
+        const size_t off_carry = ((U * Q * 4 + 255) / 256) * 256;
+        const size_t off_chain = off_carry + 2 * U * T * 16;
+        const size_t need = off_chain + (k > 1 ? U * Q * Tc * 16 : 0);
+        if (need <= kNoAllocScratchBytes) {
+            out.U = (uint32_t)U;
+            out.Q = (uint32_t)Q;
+            out.Tc = (uint32_t)Tc;
+            out.kslabs = k;
+            out.off_carry = off_carry;
+            out.off_chain = off_chain;
+            out.need = need;
+            return true;
+        }
+        if (U == 1) break;
+    }
+    return false;
 }
 
 // Scratch address for each device, looked up once with that device current.
@@ -233,40 +279,18 @@ extern "C" pe_status poly_eval_stepb_noalloc(uint64_t p, uint64_t s, uint64_t G,
         set_error("coeffs, m, group_off and out must be device pointers");
         return PE_ERR_ARG;
     }
-    // Tile choice: whole slabs per unit, as few as fit the scratch, and enough
-    // T-chunks to give every SM work.
-    const uint64_t items_target = (uint64_t)num_sms() * 16;
-    NoAllocJob J{};
-    size_t need = 0, off_carry = 0, off_chain = 0;
-    bool fits = false;
-    // At least one unit per SM (or per slab when there are fewer slabs): a
-    // larger k would leave most of the GPU idle, so such inputs are rejected.
-    const uint64_t slabs = (s + 31) / 32;
-    const uint64_t min_units = std::min<uint64_t>(slabs, (uint64_t)num_sms());
-    for (uint32_t k = 1; k <= (1u << 20) && !fits; k *= 2) {
-        const uint64_t U = (s + 32ull * k - 1) / (32ull * k);
-        if (U < min_units) break;
-        uint64_t Q = (items_target + U - 1) / U;
-        Q = std::max<uint64_t>(1, std::min<uint64_t>(Q, std::max<uint64_t>(1, T / 32)));
-        const uint64_t Tc = (T + Q - 1) / Q;
-        Q = (T + Tc - 1) / Tc;
-        off_carry = ((U * Q * 4 + 255) / 256) * 256;
-        off_chain = off_carry + 2 * U * T * 16;
-        need = off_chain + (k > 1 ? U * Q * Tc * 16 : 0);
-        if (need <= kNoAllocScratchBytes) {
-            fits = true;
-            J.U = (uint32_t)U;
-            J.Q = (uint32_t)Q;
-            J.Tc = (uint32_t)Tc;
-            J.kslabs = k;
-        }
-        if (U == 1) break;
-    }
-    if (!fits) {
+    NoAllocShape sh;
+    if (!na_plan(s, T, sh)) {
         set_error("input needs more scratch than the fixed %zu bytes (s*T too large for this entry point)",
                   kNoAllocScratchBytes);
         return PE_ERR_ARG;
     }
+    NoAllocJob J{};
+    J.U = sh.U;
+    J.Q = sh.Q;
+    J.Tc = sh.Tc;
+    J.kslabs = sh.kslabs;
+    const size_t off_carry = sh.off_carry, off_chain = sh.off_chain;
     void *base = nullptr;
     pe_status st = na_scratch(&base);
     if (st != PE_OK) return st;
@@ -290,5 +314,30 @@ extern "C" pe_status poly_eval_stepb_noalloc(uint64_t p, uint64_t s, uint64_t G,
     k_stepB_noalloc<<<(nitems + kNaWarps - 1) / kNaWarps, kNaWarps * 32, 0, cs>>>(J);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "Step B (no allocation)");
+    return PE_OK;
+}
+
+extern "C" pe_status poly_eval_stepb_noalloc_shape(uint64_t s, uint64_t T, uint32_t shape[4])
+{
+    if (!shape) {
+        set_error("shape must not be NULL");
+        return PE_ERR_ARG;
+    }
+    shape[0] = shape[1] = shape[2] = shape[3] = 0;
+    if (T == 0 || s == 0) return PE_OK;
+    if (s >= 0xffffffffull || T > (1ull << 31)) {
+        set_error("sizes out of range (need s < 2^32 - 1, T <= 2^31)");
+        return PE_ERR_ARG;
+    }
+    NoAllocShape sh;
+    if (!na_plan(s, T, sh)) {
+        set_error("input needs more scratch than the fixed %zu bytes (s*T too large for this entry point)",
+                  kNoAllocScratchBytes);
+        return PE_ERR_ARG;
+    }
+    shape[0] = sh.U;
+    shape[1] = sh.Q;
+    shape[2] = sh.Tc;
+    shape[3] = sh.kslabs;
     return PE_OK;
 }

@@ -179,7 +179,9 @@ struct pe_server {
                 r->desc.exps = r->exps.data();
             }
             pe_poly *P = nullptr;
-            pe_status st = create_poly(&r->desc, &P, false);
+            // Host-side create: its only device work is the upload copies, which
+            // do not wait for the epochs' kernels to leave the SMs.
+            pe_status st = create_poly(&r->desc, &P, false, false);
             if (st == PE_OK && !out_ok(r->T, P->G)) {   // its output could not be addressed
                 poly_eval_destroy(P);
                 P = nullptr;

@@ -1,0 +1,176 @@
+"""Every cell of every full-size workload against the oracle (GPU).
+
+The expected images are the oracle's (O1, the definition of the images,
+paper Sect. 2.3 below Eq. 1), stored as SHA-256 digests in
+tests/golden/fullsize_images.json by tests/golden/make_fullsize_digests.py,
+each tied to the digest of the inputs it was computed from.  A test hashes
+the GPU's whole output and compares: equal digests mean every cell is equal
+(tolerance zero, as the images are elements of F_p).  If the inputs generated
+here have another digest (a generator that draws differently on this host),
+the oracle is run here instead, over the host's cores (O2, which the CPU
+tests pin equal to O1, for speed).
+
+Workloads: the large one (n = 9, 10^6 terms, 5,041 Zipf groups, T = 1024)
+on every 64-bit product and the benchmark's tile shape, the same with a
+30-bit prime (32-bit product), the width pair (4*10^6 terms, T = 4096) with
+a 50-bit prime on Algorithm 2 and a 62-bit prime, the width workload with an
+NTT prime through the fast method, the real 512-job batch, and a seeded
+sample of about 1% of the requests of a served stream.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2004_11571_gb300 as pe  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_images.json")
+with open(GOLDEN) as _f:
+    DOC = json.load(_f)
+
+
+def _expected_single(name, w):
+    rec = DOC["single"].get(name)
+    if rec is not None and rec["inputs"] == wl.inputs_digest(w):
+        return rec["images"]
+    from oracle import shard
+    return wl.images_digest(shard.images(w, which="matrix")[1])
+
+
+def _expected_many(records, ws):
+    want = [r["images"] if r["inputs"] == wl.inputs_digest(w) else None for r, w in zip(records, ws)]
+    redo = [i for i, d in enumerate(want) if d is None]
+    if redo:
+        from oracle import shard
+        for i, d in zip(redo, shard.many_images([ws[i] for i in redo], which="matrix", digest_only=True)):
+            want[i] = d
+    return want
+
+
+def _digest(t):
+    return wl.images_digest(t.cpu().numpy())
+
+
+SINGLE_RUNS = {
+    "large": [("auto", None, "matrix"), ("mont64", None, "matrix"), ("barrett64", None, "matrix"),
+              ("barrett64", dict(K=16, slabs=1, tchunk=224, warps_per_block=4, tail=128), "matrix")],
+    "large30": [("auto", None, "matrix"), ("barrett64", None, "matrix")],
+    "width62": [("auto", None, "matrix"), ("mont64", None, "matrix")],
+    "width50": [("fp64", None, "matrix"), ("auto", None, "matrix")],
+    "width62ntt": [("auto", None, "fast"), ("barrett64", None, "matrix")],
+}
+MAKE = {
+    "large": lambda: wl.config_large(),
+    "large30": lambda: wl.config_large(bits=30),
+    "width62": lambda: wl.config_width(62),
+    "width50": lambda: wl.config_width(50),
+    "width62ntt": lambda: wl.config_width(62, ntt=True),
+}
+
+
+@pytest.mark.parametrize("name", list(SINGLE_RUNS))
+def test_fullsize_workload_every_cell(name):
+    w = MAKE[name]()
+    want = _expected_single(name, w)
+    for variant, tiles, method in SINGLE_RUNS[name]:
+        poly = pe.Poly.from_workload(w, variant=variant)
+        if tiles:
+            poly.set_tiles(**tiles)
+        out = torch.empty((w.T, poly.G), dtype=torch.int64, device="cuda")
+        (poly.run_fast if method == "fast" else poly.run)(w.beta, w.T, w.t0, out=out)
+        torch.cuda.synchronize()
+        assert _digest(out) == want, f"{name} {variant} {tiles} {method}: images differ from the oracle"
+        poly.close()
+        del out
+
+
+def test_batched_512_jobs_every_cell():
+    ws = wl.config_batched()
+    rec = DOC["batched"]
+    assert rec["count"] == len(ws)
+    want = _expected_many(rec["jobs"], ws)
+    polys = [pe.Poly.from_workload(w) for w in ws]
+    outs = [torch.full((w.T, p.G), -1, dtype=torch.int64, device="cuda") for w, p in zip(ws, polys)]
+    batch = pe.Batch([(p, w.beta, w.T, w.t0, o) for p, w, o in zip(polys, ws, outs)])
+    for launch in range(2):                   # a second launch reuses the graph and its scratch
+        batch.launch()
+        torch.cuda.synchronize()
+        bad = [k for k, (o, d) in enumerate(zip(outs, want)) if _digest(o) != d]
+        assert not bad, f"launch {launch}: jobs {bad[:8]} ({len(bad)} in all) differ from the oracle"
+        if launch == 0:
+            for o in outs:
+                o.fill_(-1)
+    batch.close()
+    for p in polys:
+        p.close()
+
+
+def test_served_stream_sample_every_cell():
+    # The first 1,500 requests of the served stream (the benchmark's burst):
+    # uploads and resident reuses at new points, outputs through a ring of
+    # page-locked buffers; the seeded ~1% sample is compared with the oracle
+    # cell for cell and every output is checked to lie in [0, p).
+    rec = DOC["served"]
+    pool = wl.config_batched(seed=wl.SEED_SERVE)
+    reqs = wl.served_requests(seed=wl.SEED_SERVE, pool=pool, rate=rec["rate"], duration=rec["duration"])
+    assert len(reqs) == rec["requests"]
+    n = 1500
+    sample = [r for r in rec["sample"] if r["index"] < n]
+    assert len(sample) >= n // 100
+    ws = {r["index"]: wl.served_workload(pool, reqs[r["index"]]) for r in sample}
+    want = dict(zip([r["index"] for r in sample], _expected_many(sample, [ws[r["index"]] for r in sample])))
+    G = [int(len(np.unique(w.exps[:, 0].astype(np.int64) * 65536 + w.exps[:, 1]))) for w in pool]
+    ring = torch.empty(2 << 30, dtype=torch.uint8, pin_memory=True).numpy()
+    srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
+    inflight, head, ids, got, checked = [], 0, {}, {}, 0
+
+    def retire():
+        nonlocal checked
+        i, start, nbytes, shape, t = inflight.pop(0)
+        assert srv.poll(t) == 0
+        view = ring[start:start + nbytes].view(np.uint64).reshape(shape)
+        assert int(view.max(initial=0)) < pool[reqs[i][1]].p, f"request {i}: value outside [0, p)"
+        if i in want:
+            got[i] = wl.images_digest(view)
+        checked += 1
+
+    for i in range(n):
+        _, k, beta = reqs[i]
+        w = pool[k]
+        nbytes = (w.T * G[k] * 8 + 255) // 256 * 256
+        if head + nbytes > ring.shape[0]:
+            while inflight:
+                retire()
+            head = 0
+        out = ring[head:head + w.T * G[k] * 8].view(np.uint64).reshape(w.T, G[k])
+        t = None
+        if beta is not None and k in ids:
+            try:                                   # the upload may have been evicted meanwhile
+                t, _ = srv.submit(beta, w.T, out, resident_id=ids[k])
+            except pe.PolyEvalError:
+                t = None
+        while t is None:
+            try:
+                t, ids[k] = srv.submit(w.beta if beta is None else beta, w.T, out, poly=(w.p, w.coeffs, w.exps),
+                                       borrow=True)
+            except pe.PolyEvalError as e:          # backpressure: finish the oldest request first
+                if e.status != pe.PE_ERR_ADMISSION or not inflight:
+                    raise
+                retire()
+        inflight.append((i, head, w.T * G[k] * 8, (w.T, G[k]), t))
+        head += nbytes
+    while inflight:
+        retire()
+    srv.close()
+    assert checked == n
+    bad = [i for i in want if got.get(i) != want[i]]
+    assert not bad, f"sampled requests {bad} differ from the oracle"

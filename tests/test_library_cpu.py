@@ -108,3 +108,14 @@ def test_batch_queries_validate_their_handle(L):
     assert L.poly_eval_batch_launches(None, ctypes.byref(k), ctypes.byref(n)) == 1
     assert b"NULL batch" in L.poly_eval_last_error()
     assert L.poly_eval_batch_launch(None, None) == 1
+
+
+def test_host_checks_of_query_entry_points(L):
+    """Queries reject NULL outputs and out-of-range sizes before any device call."""
+    assert L.poly_eval_stepb_noalloc_shape(1000, 64, None) == 1
+    sh = (ctypes.c_uint32 * 4)(7, 7, 7, 7)
+    assert L.poly_eval_stepb_noalloc_shape(0, 64, sh) == 0 and list(sh) == [0, 0, 0, 0]
+    assert L.poly_eval_stepb_noalloc_shape(1 << 40, 64, sh) == 1
+    assert L.poly_eval_stepb_noalloc_shape(1000, (1 << 31) + 1, sh) == 1
+    assert L.poly_eval_num_sms(None) == 1
+    assert L.poly_eval_fp64_pipe_rates(None) == 1

@@ -68,6 +68,50 @@ def test_pins_catch_mutant(name, tmp_path):
     assert not _pins_hold(lib), f"pins accepted the planted mistake: {name}"
 
 
+# Mistakes planted in O2 (the matrix method's recurrence, Sect. 2.3), caught
+# by brute force with exact integers at t0 = 1 and 3.
+O2_MUTANTS = {
+    "O2 start power off by one": ("oracle_powmod(m, t0 - 1, p)", "oracle_powmod(m, t0, p)"),
+    "O2 sums before advancing": ("v = oracle_mulmod(v, m, p);\n                sums[r] = oracle_addmod(sums[r], v, p);",
+                                 "sums[r] = oracle_addmod(sums[r], v, p);\n                v = oracle_mulmod(v, m, p);"),
+    "O2 wrong exponent column": ("tab[j][exps[i * n + 2 + j]]", "tab[j][exps[i * n + 1 + j]]"),
+    "O2 drops the coefficient": ("oracle_mulmod(coeffs[i] % p, oracle_powmod(m, t0 - 1, p), p)",
+                                 "oracle_powmod(m, t0 - 1, p)"),
+}
+
+
+def _o2_pins_hold(lib) -> bool:
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        for p in (101, 2**61 - 1):
+            for seed in range(6):
+                r = random.Random(seed)
+                w = wl.make_uniform(n=r.randint(3, 5), s=r.randint(2, 30), p=p, deg12=2, deg_rest=3, T=4,
+                                    seed=seed, sort=False)
+                for t0 in (1, 3):
+                    keys, out = oracle.eval_matrix(w, t0=t0)
+                    bk, rows = brute.eval_exact(p, w.coeffs, w.exps, w.beta, w.T, t0)
+                    if [tuple(k) for k in keys.tolist()] != bk or out.tolist() != rows:
+                        return False
+        return True
+    finally:
+        oracle._lib = saved
+
+
+def test_unmutated_o2_passes_pins():
+    assert _o2_pins_hold(oracle._load())
+
+
+@pytest.mark.parametrize("name", sorted(O2_MUTANTS))
+def test_pins_catch_o2_mutant(name, tmp_path):
+    old, new = O2_MUTANTS[name]
+    src = oracle.source()
+    assert src.count(old) == 1, name
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "mut.so"))
+    assert not _o2_pins_hold(lib), f"pins accepted the planted mistake: {name}"
+
+
 # Mistakes planted in the interpolation functions (Sect. 1), caught by the
 # closed forms for one and two terms and round trips through power sums
 # computed with exact Python integers.

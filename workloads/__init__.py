@@ -20,6 +20,7 @@ that is exact for every n < 3.3e24).
 from __future__ import annotations
 
 import dataclasses
+import hashlib
 import math
 from typing import List, Optional
 
@@ -29,7 +30,7 @@ __all__ = [
     "Workload", "is_prime", "random_prime", "make_uniform", "make_zipf",
     "config_tiny", "config_large", "config_width", "config_batched",
     "served_requests", "sort_by_group", "shuffled", "config_interp", "interp_group_sizes",
-    "random_ntt_prime",
+    "random_ntt_prime", "inputs_digest", "images_digest", "served_sample", "served_workload",
 ]
 
 MR_BASES = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
@@ -275,6 +276,22 @@ def served_requests(seed: int = SEED_SERVE, rate: float = 2000.0, duration: floa
     return reqs
 
 
+SERVED_SAMPLE_FRACTION = 0.011
+
+
+def served_sample(count: int, seed: int = SEED_SERVE + 1, frac: float = SERVED_SAMPLE_FRACTION) -> np.ndarray:
+    """Indices of a seeded sample (about `frac`, at least 1%) of the first
+    `count` requests of a served stream; the same indices for any rate."""
+    return np.flatnonzero(_rng(seed).random(count) < frac)
+
+
+def served_workload(pool: List[Workload], req) -> Workload:
+    """The evaluation a request (arrival, pool index, beta or None) asks for."""
+    _, k, beta = req
+    w = pool[k]
+    return w if beta is None else dataclasses.replace(w, beta=np.asarray(beta, dtype=np.uint64))
+
+
 def interp_group_sizes(s: int, u: int) -> np.ndarray:
     """Sizes of the (x1, x2) coefficients of a polynomial to interpolate: s terms,
     the largest coefficient exactly u terms, ceil(4s/u) coefficients whose sizes
@@ -335,3 +352,29 @@ def config_interp(seed: int = SEED_INTERP, s: int = 34_937, u: int = 9_705, n: i
     beta = _uniform_mod(rng, p, n - 2, lo=2)
     return sort_by_group(Workload(p=p, n=n, coeffs=coeffs, exps=exps, beta=beta, T=u, t0=1,
                                   name=f"interp n={n} s={s} G={G} u={u} p{bits}"))
+
+
+# ---------------------------------------------------------------------------
+# Digests: stored expected images of the full-size workloads are SHA-256 sums,
+# each tied to the exact inputs that produced it.
+# ---------------------------------------------------------------------------
+def inputs_digest(w: Workload) -> str:
+    """SHA-256 of a workload's inputs (p, n, T, t0, coefficients, exponents as
+    uint32, beta), independent of the exponent array's integer width."""
+    h = hashlib.sha256()
+    h.update(np.array([int(w.p), int(w.n), int(w.T), int(w.t0), w.s], dtype="<u8").tobytes())
+    h.update(np.ascontiguousarray(w.coeffs, dtype="<u8").tobytes())
+    h.update(np.ascontiguousarray(w.exps, dtype="<u4").tobytes())
+    h.update(np.ascontiguousarray(w.beta, dtype="<u8").tobytes())
+    return h.hexdigest()
+
+
+def images_digest(out) -> str:
+    """SHA-256 of a (T, G) image array as little-endian uint64, row-major
+    (accepts int64 or uint64 numpy arrays holding the same bits)."""
+    a = np.ascontiguousarray(np.asarray(out)).view(np.uint64)
+    a = np.ascontiguousarray(a, dtype="<u8")
+    h = hashlib.sha256()
+    h.update(np.array(a.shape, dtype="<u8").tobytes())
+    h.update(a.tobytes())
+    return h.hexdigest()
