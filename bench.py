@@ -113,21 +113,29 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-stride", type=int, default=1)
+    ap.add_argument("--terms", type=int, default=0,
+                    help="a smaller case of the same generator (profiling): terms instead of the config's")
+    ap.add_argument("--points", type=int, default=0, help="likewise, points T instead of the config's")
     return ap.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, terms=0, points=0):
+    kw = {}
+    if terms:
+        kw["s"] = terms
+    if points:
+        kw["T"] = points
     if name == "large":
-        return wl.config_large()
+        return wl.config_large(**kw)
     if name == "large30":
-        return wl.config_large(bits=30)
+        return wl.config_large(bits=30, **kw)
     if name == "tiny":
         return wl.config_tiny()
     if name == "width62":
-        return wl.config_width(62)
+        return wl.config_width(62, **kw)
     if name == "width62ntt":
-        return wl.config_width(62, ntt=True)
-    return wl.config_width(50)
+        return wl.config_width(62, ntt=True, **kw)
+    return wl.config_width(50, **kw)
 
 
 def workload_config(w, name, variant, extra=None):
@@ -622,7 +630,7 @@ def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    w = make_workload(args.config)
+    w = make_workload(args.config, args.terms, args.points)
     stride = max(args.cpu_sample_stride, 1) * 8
     for _ in range(args.warmup):
         cpu_baseline(w, stride * 8)       # untimed warm-up on a smaller sample
@@ -660,7 +668,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = make_workload(args.config)
+    w = make_workload(args.config, args.terms, args.points)
     variant = args.variant
     if variant == "auto" and args.config == "width50":
         variant = "fp64"
@@ -926,14 +934,18 @@ def run_batched(args, print_line=True):
 
 
 class PinnedRing:
-    """Page-locked host output buffers handed out in FIFO order."""
+    """Page-locked host output buffers handed out in FIFO order.
+
+    Regions are kept in allocation order.  The ring is wrapped when the newest
+    region starts below the oldest: the free space is then the gap between the
+    newest region's end and the oldest region's start; otherwise it is the
+    space after the newest region plus the space before the oldest."""
 
     def __init__(self, nbytes):
         import torch
         self.buf = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True).numpy()
         self.cap = nbytes
-        self.head = 0
-        self.regions = []   # (start, end, ticket) in allocation order
+        self.regions = []   # (start, end, tag) in allocation order
 
     def alloc(self, size, wait_oldest):
         size = (size + 255) // 256 * 256
@@ -941,23 +953,20 @@ class PinnedRing:
             raise ValueError("output larger than the ring")
         while True:
             if not self.regions:
-                self.head = 0
-                tail = 0
-            else:
-                tail = self.regions[0][0]
-            if self.head >= tail:
-                if self.cap - self.head >= size:
-                    return self.head
-                if tail >= size and (not self.regions or self.regions[0][0] >= size):
-                    return 0
-            elif tail - self.head >= size:
-                return self.head
+                return 0
+            tail, head = self.regions[0][0], self.regions[-1][1]
+            if self.regions[-1][0] < tail:           # wrapped: free is [head, tail)
+                if tail - head >= size:
+                    return head
+            elif self.cap - head >= size:            # not wrapped: after the newest ...
+                return head
+            elif tail >= size:                       # ... or before the oldest
+                return 0
             wait_oldest()
 
-    def commit(self, start, size, ticket):
+    def commit(self, start, size, tag):
         size = (size + 255) // 256 * 256
-        self.regions.append((start, start + size, ticket))
-        self.head = start + size
+        self.regions.append((start, start + size, tag))
 
     def view(self, start, shape):
         n = shape[0] * shape[1] * 8

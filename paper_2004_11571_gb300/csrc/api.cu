@@ -93,16 +93,22 @@ struct Staging {
 std::mutex g_stage_mu;
 std::vector<Staging> g_stage_free;
 
+// Best fit: the smallest cached buffer that holds n bytes, so uploads of mixed
+// sizes on several threads reuse buffers instead of pinning new ones
+// (page-locking is slow, and freeing page-locked memory waits for the device).
 Staging stage_acquire(size_t n)
 {
     {
         std::lock_guard<std::mutex> lk(g_stage_mu);
+        size_t best = g_stage_free.size();
         for (size_t i = 0; i < g_stage_free.size(); ++i)
-            if (g_stage_free[i].bytes >= n) {
-                Staging s = g_stage_free[i];
-                g_stage_free.erase(g_stage_free.begin() + i);
-                return s;
-            }
+            if (g_stage_free[i].bytes >= n && (best == g_stage_free.size() || g_stage_free[i].bytes < g_stage_free[best].bytes))
+                best = i;
+        if (best < g_stage_free.size()) {
+            Staging s = g_stage_free[best];
+            g_stage_free.erase(g_stage_free.begin() + best);
+            return s;
+        }
     }
     Staging s;
     const size_t want = std::max<size_t>(n + n / 4, 1 << 20);
@@ -143,19 +149,29 @@ void upload_stream_release(cudaStream_t s)
     g_up_streams.push_back(s);
 }
 
+// Cached page-locked bytes are kept up to a cap; above it the smallest
+// buffers are released first.
+constexpr size_t kStageCacheBytes = 4ull << 30;
+
 void stage_release(Staging s)
 {
     if (!s.p) return;
-    std::lock_guard<std::mutex> lk(g_stage_mu);
-    if (g_stage_free.size() < 16) {
+    std::vector<Staging> drop;
+    {
+        std::lock_guard<std::mutex> lk(g_stage_mu);
         g_stage_free.push_back(s);
-        return;
+        size_t total = 0;
+        for (const Staging &x : g_stage_free) total += x.bytes;
+        while (total > kStageCacheBytes && g_stage_free.size() > 1) {
+            size_t small = 0;
+            for (size_t i = 1; i < g_stage_free.size(); ++i)
+                if (g_stage_free[i].bytes < g_stage_free[small].bytes) small = i;
+            total -= g_stage_free[small].bytes;
+            drop.push_back(g_stage_free[small]);
+            g_stage_free.erase(g_stage_free.begin() + small);
+        }
     }
-    size_t small = 0;   // keep the 16 largest
-    for (size_t i = 1; i < g_stage_free.size(); ++i)
-        if (g_stage_free[i].bytes < g_stage_free[small].bytes) small = i;
-    if (g_stage_free[small].bytes < s.bytes) std::swap(g_stage_free[small], s);
-    cudaFreeHost(s.p);
+    for (const Staging &x : drop) cudaFreeHost(x.p);
 }
 }  // namespace
 
@@ -778,6 +794,54 @@ extern "C" pe_status poly_eval_debug_fail_alloc(uint32_t nth)
 
 extern "C" pe_status poly_eval_create(const pe_poly_desc *d, pe_poly **out) { return create_poly(d, out, true); }
 
+namespace {
+// One host pass over terms i0..i1: the first coefficient not below p, the
+// largest evaluated exponent, each term's (d, e) key, and whether the keys of
+// the range are in descending order (the boundary with the previous range is
+// checked by the caller).
+struct ScanOut {
+    uint32_t dmax = 0;
+    uint64_t bad = ~0ull;
+    char sorted = 1;
+};
+
+template <typename ExpT>
+void scan_terms(const ExpT *exps, const uint64_t *coeffs, uint32_t n, uint64_t p, uint64_t i0, uint64_t i1,
+                uint64_t *key, ScanOut &o)
+{
+    uint32_t dm = 0;
+    uint64_t bad = ~0ull, prev = ~0ull;
+    char srt = 1;
+    for (uint64_t i = i0; i < i1; ++i) {
+        const ExpT *e = exps + i * n;
+        if (coeffs[i] >= p && bad == ~0ull) bad = i;
+        const uint64_t k = ((uint64_t)e[0] << 32) | (uint64_t)e[1];
+        key[i] = k;
+        srt &= (char)(k <= prev);
+        prev = k;
+        for (uint32_t j = 2; j < n; ++j) dm = std::max<uint32_t>(dm, e[j]);
+    }
+    o.dmax = dm;
+    o.bad = bad;
+    o.sorted = srt;
+}
+
+// Structure-of-arrays packing of terms i0..i1 in group order (perm: the
+// source term of each position, or NULL when the input is already in order).
+template <typename ExpT, typename OutT>
+void pack_terms(const ExpT *exps, const uint64_t *coeffs, const uint32_t *perm, uint32_t n, uint64_t s,
+                uint64_t i0, uint64_t i1, uint64_t *sc, OutT *se)
+{
+    const uint32_t E = n - 2;
+    for (uint64_t i = i0; i < i1; ++i) {
+        const uint64_t o = perm ? perm[i] : i;
+        sc[i] = coeffs[o];
+        const ExpT *e = exps + o * n + 2;
+        for (uint32_t j = 0; j < E; ++j) se[(size_t)j * s + i] = (OutT)e[j];
+    }
+}
+}  // namespace
+
 pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_threads, bool allow_device)
 {
     if (!out) {
@@ -847,20 +911,16 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
     std::vector<char> t_sorted(nth, 1);
     auto scan = [&](unsigned t) {
         const uint64_t i0 = s * t / nth, i1 = s * (t + 1) / nth;
-        uint32_t dm = 0;
-        uint64_t bad = ~0ull;
-        char srt = 1;
-        for (uint64_t i = i0; i < i1; ++i) {
-            if (coeffs[i] >= d->p && bad == ~0ull) bad = i;
-            const uint64_t k = ((uint64_t)read_exp(exps, w, i * n) << 32) | read_exp(exps, w, i * n + 1);
-            key[i] = k;
-            for (uint32_t j = 2; j < n; ++j) dm = std::max(dm, read_exp(exps, w, i * n + j));
-        }
-        for (uint64_t i = std::max<uint64_t>(i0, 1); i < i1; ++i)
-            if (key[i] > key[i - 1]) srt = 0;
-        t_dmax[t] = dm;
-        t_bad[t] = bad;
-        t_sorted[t] = srt;
+        ScanOut o;
+        if (w == 1)
+            scan_terms((const uint8_t *)exps, coeffs, n, d->p, i0, i1, key, o);
+        else if (w == 2)
+            scan_terms((const uint16_t *)exps, coeffs, n, d->p, i0, i1, key, o);
+        else
+            scan_terms((const uint32_t *)exps, coeffs, n, d->p, i0, i1, key, o);
+        t_dmax[t] = o.dmax;
+        t_bad[t] = o.bad;
+        t_sorted[t] = o.sorted;
     };
     auto parallel = [&](auto fn) {
         const std::function<void(unsigned)> f = fn;
@@ -927,17 +987,22 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
     unsigned char *stage = stg.p ? (unsigned char *)stg.p : fallback.data();
     uint64_t *sc = (uint64_t *)stage;
     uint8_t *se = stage + s * 8;
+    const uint32_t *pm = sorted ? nullptr : perm.data();
     auto pack = [&](unsigned t) {
         const uint64_t i0 = s * t / nth, i1 = s * (t + 1) / nth;
-        for (uint64_t i = i0; i < i1; ++i) {
-            const uint64_t o = src(i);
-            sc[i] = coeffs[o];
-            if (P->exp_bytes == 1)
-                for (uint32_t j = 0; j < E; ++j) se[(size_t)j * s + i] = (uint8_t)read_exp(exps, w, o * n + 2 + j);
-            else
-                for (uint32_t j = 0; j < E; ++j)
-                    ((uint16_t *)se)[(size_t)j * s + i] = (uint16_t)read_exp(exps, w, o * n + 2 + j);
-        }
+        const bool out8 = P->exp_bytes == 1;
+        if (w == 1 && out8)
+            pack_terms((const uint8_t *)exps, coeffs, pm, n, s, i0, i1, sc, se);
+        else if (w == 1)
+            pack_terms((const uint8_t *)exps, coeffs, pm, n, s, i0, i1, sc, (uint16_t *)se);
+        else if (w == 2 && out8)
+            pack_terms((const uint16_t *)exps, coeffs, pm, n, s, i0, i1, sc, se);
+        else if (w == 2)
+            pack_terms((const uint16_t *)exps, coeffs, pm, n, s, i0, i1, sc, (uint16_t *)se);
+        else if (out8)
+            pack_terms((const uint32_t *)exps, coeffs, pm, n, s, i0, i1, sc, se);
+        else
+            pack_terms((const uint32_t *)exps, coeffs, pm, n, s, i0, i1, sc, (uint16_t *)se);
     };
     parallel(pack);
     cudaError_t e;

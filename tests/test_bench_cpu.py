@@ -31,3 +31,33 @@ def test_reference_arm_other_ranks_exit_quietly():
                         "--gpus", "2", "--steps", "2", "--warmup", "3"], capture_output=True, text=True,
                        timeout=600, cwd=ROOT, env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_output_ring_never_hands_out_a_live_region():
+    """The served benchmark's page-locked output ring, driven with random sizes
+    and random completions: live regions never overlap and stay inside the ring
+    (a wrapped ring filled exactly to its oldest region must read as full)."""
+    import random
+    sys.path.insert(0, ROOT)
+    import bench
+    ring = bench.PinnedRing.__new__(bench.PinnedRing)     # no page-locked buffer needed
+    ring.cap, ring.regions = 64 * 256, []
+    rnd = random.Random(7)
+
+    def wait_oldest():
+        ring.regions.pop(0)
+
+    exact_fills = 0
+    for step in range(20000):
+        size = rnd.choice([256, 512, 768, 1024, 4096, 256 * rnd.randint(1, 64)])
+        start = ring.alloc(size, wait_oldest)
+        end = start + (size + 255) // 256 * 256
+        assert 0 <= start and end <= ring.cap
+        for s0, e0, _ in ring.regions:
+            assert end <= s0 or start >= e0, (step, start, end, ring.regions)
+        if ring.regions and ring.regions[-1][0] < ring.regions[0][0] and end == ring.regions[0][0]:
+            exact_fills += 1
+        ring.commit(start, size, step)
+        while ring.regions and rnd.random() < 0.3:
+            wait_oldest()
+    assert exact_fills > 0          # the case that must read as full did occur

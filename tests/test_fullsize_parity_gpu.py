@@ -114,11 +114,13 @@ def test_batched_512_jobs_every_cell():
         p.close()
 
 
-def test_served_stream_sample_every_cell():
+@pytest.mark.parametrize("cap_gb", [40, 2])
+def test_served_stream_sample_every_cell(cap_gb):
     # The first 1,500 requests of the served stream (the benchmark's burst):
     # uploads and resident reuses at new points, outputs through a ring of
     # page-locked buffers; the seeded ~1% sample is compared with the oracle
-    # cell for cell and every output is checked to lie in [0, p).
+    # cell for cell and every output is checked to lie in [0, p).  With a
+    # 2 GB cap the server evicts uploads and re-uploads them while epochs run.
     rec = DOC["served"]
     pool = wl.config_batched(seed=wl.SEED_SERVE)
     reqs = wl.served_requests(seed=wl.SEED_SERVE, pool=pool, rate=rec["rate"], duration=rec["duration"])
@@ -130,7 +132,7 @@ def test_served_stream_sample_every_cell():
     want = dict(zip([r["index"] for r in sample], _expected_many(sample, [ws[r["index"]] for r in sample])))
     G = [int(len(np.unique(w.exps[:, 0].astype(np.int64) * 65536 + w.exps[:, 1]))) for w in pool]
     ring = torch.empty(2 << 30, dtype=torch.uint8, pin_memory=True).numpy()
-    srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
+    srv = pe.Server(mem_cap_bytes=cap_gb << 30, streams=2, max_epoch_jobs=64)
     inflight, head, ids, got, checked = [], 0, {}, {}, 0
 
     def retire():
@@ -170,7 +172,10 @@ def test_served_stream_sample_every_cell():
         head += nbytes
     while inflight:
         retire()
+    evictions = srv.stats()["evictions"]
     srv.close()
     assert checked == n
+    if cap_gb == 2:
+        assert evictions > 0
     bad = [i for i in want if got.get(i) != want[i]]
     assert not bad, f"sampled requests {bad} differ from the oracle"
