@@ -842,6 +842,79 @@ void pack_terms(const ExpT *exps, const uint64_t *coeffs, const uint32_t *perm, 
 }
 }  // namespace
 
+// Allocates a new handle's device arrays and uploads its packed terms
+// (coefficients, then E rows of exponents) from `stage`: the allocations and
+// both copies are queued on one upload stream and waited for once.  Releases
+// the staging buffer; deletes P on failure.
+static pe_status upload_packed(pe_poly *P, Staging stg, const unsigned char *stage, size_t se_bytes)
+{
+    const uint64_t s = P->s;
+    const size_t dp1 = P->dmax + 1;
+    cudaStream_t us = upload_stream_acquire();
+    cudaError_t e;
+    if ((e = P->coeffs.ensure_async(s * 8, us)) != cudaSuccess || (e = P->exps->ensure_async(se_bytes, us)) != cudaSuccess ||
+        (e = P->mR.ensure_async(s * 8, us)) != cudaSuccess ||
+        (e = P->ptab.ensure_async((size_t)P->E * dp1 * 8, us)) != cudaSuccess) {
+        cudaStreamSynchronize(us);
+        upload_stream_release(us);
+        stage_release(stg);
+        delete P;
+        return cuda_fail(e, "device allocation");
+    }
+    if ((s && (e = cudaMemcpyAsync(P->coeffs.p, stage, s * 8, cudaMemcpyHostToDevice, us)) != cudaSuccess) ||
+        (se_bytes && (e = cudaMemcpyAsync(P->exps->p, stage + s * 8, se_bytes, cudaMemcpyHostToDevice, us)) != cudaSuccess) ||
+        (e = cudaStreamSynchronize(us)) != cudaSuccess) {
+        cudaStreamSynchronize(us);
+        upload_stream_release(us);
+        stage_release(stg);
+        delete P;
+        return cuda_fail(e, "uploading terms");
+    }
+    upload_stream_release(us);
+    stage_release(stg);
+    return PE_OK;
+}
+
+namespace {
+// One pass over terms with byte exponents that are already in group order
+// (descending (d, e)): checks the coefficients, records the groups and packs
+// coefficients and exponent rows into staging.  Returns false as soon as a
+// key rises (the input is not in group order; the caller sorts instead).
+bool scan_pack_sorted_u8(const uint64_t *coeffs, const uint8_t *exps, uint32_t n, uint64_t s, uint64_t p,
+                         uint64_t *sc, uint8_t *se, std::vector<uint64_t> &goff, std::vector<uint32_t> &keys,
+                         uint32_t &dmax, uint64_t &bad)
+{
+    const uint32_t E = n - 2;
+    uint64_t prev = ~0ull;
+    uint32_t dm = 0;
+    bad = ~0ull;
+    goff.assign(1, 0);
+    keys.clear();
+    for (uint64_t i = 0; i < s; ++i) {
+        const uint8_t *e = exps + i * n;
+        const uint64_t c = coeffs[i];
+        if (c >= p && bad == ~0ull) bad = i;
+        sc[i] = c;
+        const uint64_t k = ((uint64_t)e[0] << 32) | (uint64_t)e[1];
+        if (k != prev) {
+            if (i && k > prev) return false;
+            if (i) goff.push_back(i);
+            keys.push_back(e[0]);
+            keys.push_back(e[1]);
+            prev = k;
+        }
+        for (uint32_t j = 0; j < E; ++j) {
+            const uint8_t x = e[2 + j];
+            dm = std::max<uint32_t>(dm, x);
+            se[(size_t)j * s + i] = x;
+        }
+    }
+    goff.push_back(s);
+    dmax = dm;
+    return true;
+}
+}  // namespace
+
 pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_threads, bool allow_device)
 {
     if (!out) {
@@ -906,6 +979,44 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
     uint64_t *key = key_buf.get();
     const unsigned nth = host_threads && s >= (1u << 18)
                              ? std::max(1u, std::min(8u, std::thread::hardware_concurrency())) : 1u;
+    if (w == 1 && nth == 1 && s && n > 2) {
+        // Byte exponents in group order (the usual input): one pass.
+        Staging stg = stage_acquire(s * 8 + (size_t)(n - 2) * s);
+        if (stg.p) {
+            unsigned char *stage = (unsigned char *)stg.p;
+            std::vector<uint64_t> goff;
+            std::vector<uint32_t> gkeys;
+            uint32_t dm = 0;
+            uint64_t bad = ~0ull;
+            if (scan_pack_sorted_u8(coeffs, (const uint8_t *)exps, n, s, d->p, (uint64_t *)stage, stage + s * 8, goff,
+                                    gkeys, dm, bad)) {
+                if (bad != ~0ull) {
+                    stage_release(stg);
+                    set_error("coefficient %llu of term %llu is not reduced mod p", (unsigned long long)coeffs[bad],
+                              (unsigned long long)bad);
+                    return PE_ERR_NOT_REDUCED;
+                }
+                pe_poly *P = new pe_poly();
+                P->p = d->p;
+                P->n = n;
+                P->E = E;
+                P->s = s;
+                P->requested_variant = variant;
+                P->variant = variant == PE_MODMUL_AUTO ? default_variant(d->p) : variant;
+                P->mc = make_modctx(d->p);
+                P->dmax = dm;
+                P->exp_bytes = 1;
+                P->group_off = std::move(goff);
+                P->keys = std::move(gkeys);
+                P->G = P->keys.size() / 2;
+                const pe_status ust = upload_packed(P, stg, stage, (size_t)E * s);
+                if (ust != PE_OK) return ust;
+                *out = P;
+                return PE_OK;
+            }
+            stage_release(stg);
+        }
+    }
     std::vector<uint32_t> t_dmax(nth, 0);
     std::vector<uint64_t> t_bad(nth, ~0ull);
     std::vector<char> t_sorted(nth, 1);
@@ -1005,26 +1116,8 @@ pe_status pe::create_poly(const pe_poly_desc *d, pe_poly **out, bool host_thread
             pack_terms((const uint32_t *)exps, coeffs, pm, n, s, i0, i1, sc, (uint16_t *)se);
     };
     parallel(pack);
-    cudaError_t e;
-    const size_t dp1 = dmax + 1;
-    cudaStream_t us = upload_stream_acquire();
-    if ((e = P->coeffs.ensure(s * 8, us)) != cudaSuccess || (e = P->exps->ensure(se_bytes, us)) != cudaSuccess ||
-        (e = P->mR.ensure(s * 8, us)) != cudaSuccess || (e = P->ptab.ensure((size_t)E * dp1 * 8, us)) != cudaSuccess) {
-        upload_stream_release(us);
-        stage_release(stg);
-        delete P;
-        return cuda_fail(e, "device allocation");
-    }
-    if ((s && (e = cudaMemcpyAsync(P->coeffs.p, sc, s * 8, cudaMemcpyHostToDevice, us)) != cudaSuccess) ||
-        (se_bytes && (e = cudaMemcpyAsync(P->exps->p, se, se_bytes, cudaMemcpyHostToDevice, us)) != cudaSuccess) ||
-        (e = cudaStreamSynchronize(us)) != cudaSuccess) {
-        upload_stream_release(us);
-        stage_release(stg);
-        delete P;
-        return cuda_fail(e, "uploading terms");
-    }
-    upload_stream_release(us);
-    stage_release(stg);
+    const pe_status ust = upload_packed(P, stg, stage, se_bytes);
+    if (ust != PE_OK) return ust;
     if (!sorted) P->perm = std::make_shared<const std::vector<uint32_t>>(std::move(perm));
     *out = P;
     return PE_OK;
@@ -1162,7 +1255,8 @@ extern "C" pe_status poly_eval_set_tiles(pe_poly *P, const pe_tiles *t)
     return PE_OK;
 }
 
-static pe_status plan_for(pe_poly *P, uint64_t T, Tiles *tiles, cudaStream_t st = nullptr, bool queued = false)
+// The product and tile shape of a run of T points (cheap: no plan tables).
+static Tiles plan_tiles(pe_poly *P, uint64_t T)
 {
     const int v = run_variant(P, T);
     if (v != P->variant) {
@@ -1170,18 +1264,30 @@ static pe_status plan_for(pe_poly *P, uint64_t T, Tiles *tiles, cudaStream_t st 
         P->plan.valid = false;
         P->tail_plan.valid = false;
     }
-    *tiles = choose_tiles(P, T, &P->forced);
-    if (P->tailT != tiles->tailT) {
+    const Tiles tiles = choose_tiles(P, T, &P->forced);
+    if (P->tailT != tiles.tailT) {
         P->plan.valid = false;
         P->tail_plan.valid = false;
-        P->tailT = tiles->tailT;
+        P->tailT = tiles.tailT;
     }
-    pe_status ps = ensure_plan(P, P->plan, *tiles, T - tiles->tailT, st, queued);
-    if (ps != PE_OK || !tiles->tailT) return ps;
-    Tiles tt = *tiles;
+    return tiles;
+}
+
+// The plans (chunk, unit and span tables, scratch) of both bands for `tiles`.
+static pe_status plan_build(pe_poly *P, uint64_t T, const Tiles &tiles, cudaStream_t st, bool queued)
+{
+    pe_status ps = ensure_plan(P, P->plan, tiles, T - tiles.tailT, st, queued);
+    if (ps != PE_OK || !tiles.tailT) return ps;
+    Tiles tt = tiles;
     tt.kslabs = 1;
-    tt.Tc = tail_tc(tiles->tailT);
-    return ensure_plan(P, P->tail_plan, tt, tiles->tailT, st, queued);
+    tt.Tc = tail_tc(tiles.tailT);
+    return ensure_plan(P, P->tail_plan, tt, tiles.tailT, st, queued);
+}
+
+static pe_status plan_for(pe_poly *P, uint64_t T, Tiles *tiles, cudaStream_t st = nullptr, bool queued = false)
+{
+    *tiles = plan_tiles(P, T);
+    return plan_build(P, T, *tiles, st, queued);
 }
 
 extern "C" pe_status poly_eval_plan_info(pe_poly *P, uint64_t T, pe_plan_info *info)
@@ -1276,6 +1382,50 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
     return run_matrix(P, beta, T, t0, out, stream);
 }
 
+constexpr uint64_t kPipelinedDownloadBytes = 16ull << 20;
+
+// Step B into host memory: one launch per T-chunk (main band, then tail
+// band), alternating between the run's stream and the handle's second stream,
+// each followed by the download of the rows it wrote.  Items of a later chunk
+// fill the SMs as an earlier chunk's items finish (launches on two streams
+// overlap), and each chunk's copy runs while the later chunks compute, so most
+// of the download is hidden.  T-chunks share nothing but read-only plan
+// tables: carries and arrival counters are per T-chunk, chain buffers per item.
+static pe_status stepb_download_pipelined(pe_poly *P, const Tiles &t, StepBJob J0, StepBJob J1, uint64_t T0,
+                                          uint64_t T, uint64_t *out, uint64_t *out_dev, cudaStream_t cs)
+{
+    cudaError_t e;
+    if (!P->aux && (e = cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "second stream");
+    if ((!P->fork_ev && (e = cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming)) != cudaSuccess) ||
+        (!P->join_ev && (e = cudaEventCreateWithFlags(&P->join_ev, cudaEventDisableTiming)) != cudaSuccess))
+        return cuda_fail(e, "events");
+    if ((e = cudaEventRecord(P->fork_ev, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(P->aux, P->fork_ev, 0)) != cudaSuccess)
+        return cuda_fail(e, "fork");
+    const uint64_t G = P->G;
+    const StepBJob none{};
+    uint32_t k = 0;
+    for (int band = 0; band < 2; ++band) {
+        const Plan &pl = band == 0 ? P->plan : P->tail_plan;
+        StepBJob J = band == 0 ? J0 : J1;
+        const uint64_t rows = band == 0 ? T0 : T - T0, row0 = band == 0 ? 0 : T0;
+        if (!rows) continue;
+        for (uint32_t q = 0; q < pl.Q; ++q, ++k) {
+            cudaStream_t st = (k & 1) ? P->aux : cs;
+            J.item0 = q * pl.U;
+            if ((e = launch_stepB((int)t.K, P->variant, J, pl.U, none, 0, (int)t.wpb, st)) != cudaSuccess)
+                return cuda_fail(e, "Step B");
+            const uint64_t r0 = row0 + (uint64_t)q * pl.Tc, r1 = std::min<uint64_t>(row0 + rows, r0 + pl.Tc);
+            if ((e = cudaMemcpyAsync(out + r0 * G, out_dev + r0 * G, (r1 - r0) * G * 8, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess)
+                return cuda_fail(e, "copy back");
+        }
+    }
+    if ((e = cudaEventRecord(P->join_ev, P->aux)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, P->join_ev, 0)) != cudaSuccess)
+        return cuda_fail(e, "join");
+    return PE_OK;
+}
+
 pe_status pe::run_matrix(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t t0, uint64_t *out, void *stream)
 {
     if (!P) {
@@ -1299,12 +1449,15 @@ pe_status pe::run_matrix(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t 
         cudaStreamWaitEvent(cs, P->last_use, 0);
         cudaStreamWaitEvent(alloc_stream(), P->last_use, 0);
     }
-    Tiles t;
-    if ((st = plan_for(P, T, &t, cs, true)) != PE_OK) return st;
+    // Tiles first: the power tables and Step A need only the start rows, so
+    // they are queued before the plan tables are built on the host.
+    const Tiles t = plan_tiles(P, T);
     cudaPointerAttributes attr{};
-    bool dev_out = false;
-    if (cudaPointerGetAttributes(&attr, out) == cudaSuccess)
+    bool dev_out = false, pinned_out = false;
+    if (cudaPointerGetAttributes(&attr, out) == cudaSuccess) {
         dev_out = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+        pinned_out = attr.type == cudaMemoryTypeHost;
+    }
     cudaGetLastError();
     uint64_t *out_dev = out;
     cudaError_t e;
@@ -1330,14 +1483,16 @@ pe_status pe::run_matrix(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t 
     if ((e = launch_powtab(barg, P->E, dp1, P->mc, P->ptab.as<uint64_t>(), cs)) != cudaSuccess)
         return cuda_fail(e, "power tables");
     mark(1);
-    // Item start rows: band 0's T-chunks, then the tail band's.
+    // Item start rows: band 0's T-chunks, then the tail band's (the plans'
+    // T-chunks follow from the tiles alone).
     const uint64_t T0 = T - t.tailT;
+    const uint32_t tc0 = t.Tc, tc1 = t.tailT ? tail_tc(t.tailT) : 1;
+    const uint32_t q0 = (uint32_t)((T0 + tc0 - 1) / tc0), q1 = t.tailT ? (uint32_t)((t.tailT + tc1 - 1) / tc1) : 0;
     StartRows sr{};
-    const uint32_t q0 = P->plan.Q, q1 = t.tailT ? P->tail_plan.Q : 0;
     bool use_starts = q0 + q1 <= (uint32_t)kMaxStarts;
     if (use_starts) {
-        for (uint32_t q = 0; q < q0; ++q) sr.row[sr.n++] = q * P->plan.Tc;
-        for (uint32_t q = 0; q < q1; ++q) sr.row[sr.n++] = (uint32_t)T0 + q * P->tail_plan.Tc;
+        for (uint32_t q = 0; q < q0; ++q) sr.row[sr.n++] = q * tc0;
+        for (uint32_t q = 0; q < q1; ++q) sr.row[sr.n++] = (uint32_t)T0 + q * tc1;
         use_starts = plan_start_gaps(&sr);   // at most three distinct gaps (main band, band change, tail band)
     }
     if (use_starts) {
@@ -1350,6 +1505,11 @@ pe_status pe::run_matrix(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t 
                          P->mR.as<uint64_t>(), num_sms(), cs);
     }
     if (e != cudaSuccess) return cuda_fail(e, "Step A");
+    if ((st = plan_build(P, T, t, cs, true)) != PE_OK) return st;
+    if (P->plan.Q != q0 || (t.tailT && P->tail_plan.Q != q1)) {
+        set_error("internal: plan and start rows disagree");
+        return PE_ERR_ARG;
+    }
     StepBJob J0 = make_job(P, P->plan, t0, out_dev, false);
     StepBJob J1{};
     uint32_t n1 = 0;
@@ -1363,16 +1523,23 @@ pe_status pe::run_matrix(pe_poly *P, const uint64_t *beta, uint64_t T, uint64_t 
         J1.vs_base = q0;
     }
     mark(2);
-    if ((e = launch_stepB((int)t.K, P->variant, J0, P->plan.U * P->plan.Q, J1, n1, (int)t.wpb, cs)) != cudaSuccess)
-        return cuda_fail(e, "Step B");
+    // A large download into page-locked host memory overlaps the compute
+    // chunk by chunk; small ones take one launch and one copy (extra launches
+    // would cost more than the copy), and so do downloads into pageable memory
+    // (a copy there returns only when it is done, which would stall the launches).
+    const bool pipelined = pinned_out && T * P->G * 8 >= kPipelinedDownloadBytes && q0 + q1 >= 3;
+    if (!pipelined) {
+        if ((e = launch_stepB((int)t.K, P->variant, J0, P->plan.U * P->plan.Q, J1, n1, (int)t.wpb, cs)) != cudaSuccess)
+            return cuda_fail(e, "Step B");
+        if (!dev_out && (e = cudaMemcpyAsync(out, out_dev, T * P->G * 8, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+            return cuda_fail(e, "copy back");
+    } else if ((st = stepb_download_pipelined(P, t, J0, J1, T0, T, out, out_dev, cs)) != PE_OK) {
+        return st;
+    }
     mark(3);
     if (!P->last_use && (e = cudaEventCreateWithFlags(&P->last_use, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "event");
     if ((e = cudaEventRecord(P->last_use, cs)) != cudaSuccess) return cuda_fail(e, "event");
-    if (!dev_out) {
-        if ((e = cudaMemcpyAsync(out, out_dev, T * P->G * 8, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
-            return cuda_fail(e, "copy back");
-        if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "run");
-    }
+    if (!dev_out && (e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "run");
     return PE_OK;
 }

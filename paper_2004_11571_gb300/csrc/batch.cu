@@ -252,11 +252,22 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
         o_chain[j] = S.take(ph[j].chain_bytes());
         o_ptab[j] = S.take((size_t)std::max<uint32_t>(P->E, 1) * dp1c[j] * 8);
     }
-    // Items, ordered by decreasing cost (a slab-point of a K-term chunk costs K).
-    std::vector<std::pair<double, uint2>> items;
+    // Items, grouped by code path (K and product: the warps of an SM then run
+    // the same instantiation of the item loop and share its instructions),
+    // classes in decreasing order of their largest item, each by decreasing
+    // cost (a slab-point of a K-term chunk costs K), so the queue ends on the
+    // cheapest items.
+    struct QItem {
+        double cost;
+        uint32_t cls;
+        uint2 it;
+    };
+    std::vector<QItem> items;
+    std::map<uint32_t, double> cls_max;
     for (size_t j = 0; j < njobs; ++j) {
         if (!queued(j)) continue;
         const PlanHost &p = ph[j];
+        const uint32_t cls = p.K * 8 + (uint32_t)var[j];
         const double lg = std::log2((double)std::max<uint64_t>(2, jobs[j].t0 + jobs[j].T));
         for (uint32_t q = 0; q < p.Q; ++q) {
             const uint64_t tc = std::min<uint64_t>(p.Tc, p.T - (uint64_t)q * p.Tc);
@@ -264,11 +275,18 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
                 const uint32_t chunks = std::min(p.NC - u * 32 * p.kslabs, 32 * p.kslabs);
                 const double slabs = std::ceil(chunks / 32.0);
                 const double cost = slabs * 32.0 * (p.K * (double)tc * 1.2 + (double)tc * 0.7 + p.K * lg * 3.0);
-                items.push_back({cost, make_uint2((uint32_t)j, q * p.U + u)});
+                items.push_back({cost, cls, make_uint2((uint32_t)j, q * p.U + u)});
+                cls_max[cls] = std::max(cls_max[cls], cost);
             }
         }
     }
-    std::stable_sort(items.begin(), items.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::stable_sort(items.begin(), items.end(), [&](const QItem &a, const QItem &b) {
+        if (a.cls != b.cls) {
+            const double ma = cls_max[a.cls], mb = cls_max[b.cls];
+            return ma != mb ? ma > mb : a.cls > b.cls;
+        }
+        return a.cost > b.cost;
+    });
     const size_t off_items = U.take(std::max<size_t>(items.size(), 1) * sizeof(uint2));
     // Counters (and the queue head) in one contiguous scratch block, cleared before each launch.
     const size_t cnt0 = S.off;
@@ -324,7 +342,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
     img.off_pow = off_pow;
     img.ptab_off = o_ptab;
     std::vector<uint2> it(items.size());
-    for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
+    for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].it;
     put(off_items, it.data(), it.size() * sizeof(uint2));
     img.base = base;
     img.d_jobs = (StepBJob *)(base + off_jobs);

@@ -51,6 +51,7 @@ struct StepBJob {
     uint32_t K, var;          // lane chunk size and modular product (queue dispatch)
     const uint64_t *vstart;   // L x s starting values a_i m_i^t per item start row, or nullptr (jump start)
     uint32_t vs_base;         // row of vstart used by T-chunk 0 of this job
+    uint32_t item0;           // first work item of this launch (plain kernel: one launch per T-chunk)
     ModCtx mc;
 };
 

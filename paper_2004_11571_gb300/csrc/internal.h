@@ -197,10 +197,17 @@ struct pe_poly {
     std::vector<cudaEvent_t> events;   // 4 per timed run
     size_t events_used = 0;
     cudaEvent_t last_use = nullptr;    // end of the latest run; frees of this handle's buffers wait for it
+    // Second stream of a run into host memory (T-chunks alternate between the
+    // run's stream and this one), with its fork and join events.
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     ~pe_poly()
     {
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         if (last_use) cudaEventDestroy(last_use);
+        if (fork_ev) cudaEventDestroy(fork_ev);
+        if (join_ev) cudaEventDestroy(join_ev);
+        if (aux) cudaStreamDestroy(aux);
     }
     uint64_t device_bytes() const
     {

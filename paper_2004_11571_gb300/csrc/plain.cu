@@ -79,9 +79,9 @@ __global__ void __launch_bounds__(128, (K >= 16 ? 3 : K >= 12 ? 4 : 5)) k_stepB(
     const uint32_t warp = threadIdx.x >> 5;
     const uint32_t item = blockIdx.x * (blockDim.x >> 5) + warp;
     if (item < n0)
-        stepb_item<K, VAR>(J0, item, sm[warp]);
+        stepb_item<K, VAR>(J0, J0.item0 + item, sm[warp]);
     else if (item - n0 < n1)
-        stepb_item<K, VAR>(J1, item - n0, sm[warp]);
+        stepb_item<K, VAR>(J1, J1.item0 + (item - n0), sm[warp]);
 }
 
 cudaError_t launch_powtab(const BetaArg &beta, uint32_t E, uint32_t dp1, const ModCtx &mc, uint64_t *ptab,

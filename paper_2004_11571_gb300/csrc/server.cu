@@ -102,6 +102,14 @@ struct pe_server {
     double t_upload = 0.0, t_plan = 0.0, t_launch = 0.0, t_finish = 0.0;
     Clock::time_point busy_since;
     int inflight = 0;
+    bool shrink_wanted = false;        // set by an upload that cannot fit while nothing runs
+
+    uint64_t slot_bytes() const
+    {
+        uint64_t b = 0;
+        for (uint32_t i = 0; i < nslots; ++i) b += slots[i].arena.bytes + slots[i].outs.bytes;
+        return b;
+    }
 
     uint64_t committed() const
     {
@@ -160,6 +168,14 @@ struct pe_server {
             SrvRequest *r = backlog.front();
             const uint64_t need = poly_bytes_estimate(r->desc);
             if (!make_room(need)) {
+                if (uploading == 0 && inflight == 0 && ready.empty() && slot_bytes() > 0) {
+                    // Nothing runs: the epoch thread gives back the idle
+                    // epochs' scratch (it grows again on demand), then retry.
+                    shrink_wanted = true;
+                    cv_work.notify_all();
+                    cv_upload.wait_for(lk, std::chrono::milliseconds(1));
+                    continue;
+                }
                 if (uploading == 0 && inflight == 0 && ready.empty()) {   // can never fit
                     backlog.pop_front();
                     ++rejected;
@@ -293,6 +309,11 @@ struct pe_server {
             jobs[j].out = (uint64_t *)(s.outs.as<unsigned char>() + r->out_off);
             s.term_points += (double)r->poly->s * (double)r->T;
         }
+        // Every request runs in the epoch's queue kernel.  (Running requests of
+        // at least 2^28 term-points as plain runs after it, as a batch does,
+        // measured slower: 2,700-3,200 against 3,400-4,900 requests/s on bursts
+        // of the served mixture; the large requests then stop sharing the SMs
+        // with the small ones and each epoch ends on a lone plain run.)
         pe_status st = batch_build(jobs.data(), jobs.size(), s.arena, s.img, false);
         t_plan += since(t_pl0);
         const Clock::time_point t_la0 = Clock::now();
@@ -336,6 +357,15 @@ struct pe_server {
             for (uint32_t i = 0; i < nslots; ++i)
                 if (!slots[i].busy && launch(slots[i])) progressed = true;
             std::unique_lock<std::mutex> lk(mu);
+            if (shrink_wanted) {   // an upload cannot fit: release idle slots' device scratch
+                shrink_wanted = false;
+                for (uint32_t i = 0; i < nslots; ++i)
+                    if (!slots[i].busy) {
+                        slots[i].arena.release();
+                        slots[i].outs.release();
+                    }
+                cv_upload.notify_all();
+            }
             bool any_busy = false;
             for (uint32_t i = 0; i < nslots; ++i) any_busy |= slots[i].busy;
             if (stop && backlog.empty() && ready.empty() && uploading == 0 && !any_busy) return;

@@ -62,7 +62,8 @@ def _digest(t):
 
 SINGLE_RUNS = {
     "large": [("auto", None, "matrix"), ("mont64", None, "matrix"), ("barrett64", None, "matrix"),
-              ("barrett64", dict(K=16, slabs=1, tchunk=224, warps_per_block=4, tail=128), "matrix")],
+              ("barrett64", dict(K=16, slabs=1, tchunk=224, warps_per_block=4, tail=128), "matrix"),
+              ("auto", None, "host_pinned"), ("barrett64", None, "host_pageable")],
     "large30": [("auto", None, "matrix"), ("barrett64", None, "matrix")],
     "width62": [("auto", None, "matrix"), ("mont64", None, "matrix")],
     "width50": [("fp64", None, "matrix"), ("auto", None, "matrix")],
@@ -85,8 +86,13 @@ def test_fullsize_workload_every_cell(name):
         poly = pe.Poly.from_workload(w, variant=variant)
         if tiles:
             poly.set_tiles(**tiles)
-        out = torch.empty((w.T, poly.G), dtype=torch.int64, device="cuda")
-        (poly.run_fast if method == "fast" else poly.run)(w.beta, w.T, w.t0, out=out)
+        if method.startswith("host"):      # into host memory: the download overlaps the compute by T-chunk
+            pinned = method == "host_pinned"
+            out = torch.full((w.T, poly.G), -1, dtype=torch.int64, pin_memory=pinned)
+            poly.run(w.beta, w.T, w.t0, out=out.numpy())
+        else:
+            out = torch.empty((w.T, poly.G), dtype=torch.int64, device="cuda")
+            (poly.run_fast if method == "fast" else poly.run)(w.beta, w.T, w.t0, out=out)
         torch.cuda.synchronize()
         assert _digest(out) == want, f"{name} {variant} {tiles} {method}: images differ from the oracle"
         poly.close()
