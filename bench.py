@@ -113,6 +113,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-stride", type=int, default=1)
+    ap.add_argument("--split", default="weak", choices=["weak", "strong", "group"],
+                    help="N > 1: weak = each rank its own block of T points; strong = the T points split into "
+                         "contiguous blocks; group = contiguous ranges of (x1,x2) groups (whole output columns)")
     ap.add_argument("--terms", type=int, default=0,
                     help="a smaller case of the same generator (profiling): terms instead of the config's")
     ap.add_argument("--points", type=int, default=0, help="likewise, points T instead of the config's")
@@ -198,6 +201,44 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def rank_share(w, split, rank, world):
+    """The part of workload `w` that rank `rank` of `world` evaluates, as
+    (workload, first point, points, scaling).  No exchange is needed in any
+    split (the images of different points and of different groups are
+    independent): weak gives every rank T points of its own, strong splits the
+    T points into contiguous blocks, group gives each rank the sub-polynomial
+    of a contiguous range of (x1,x2) groups with about equal terms."""
+    from paper_2004_11571_gb300 import sharding
+    if world == 1 or split == "weak":
+        t0, T = sharding.weak_block(int(w.T), w.t0, rank)
+        return w, t0, T, "weak"
+    if split == "strong":
+        t0, T = sharding.strong_block(int(w.T), w.t0, rank, world)
+        return w, t0, T, "strong"
+    key = w.exps[:, 0].astype(np.int64) * (1 << 32) + w.exps[:, 1].astype(np.int64)
+    if np.any(key[1:] > key[:-1]):
+        w = wl.sort_by_group(w)
+        key = w.exps[:, 0].astype(np.int64) * (1 << 32) + w.exps[:, 1].astype(np.int64)
+    starts = np.flatnonzero(np.concatenate([[True], key[1:] != key[:-1]])) if w.s else np.zeros(0, np.int64)
+    off = np.concatenate([starts, [w.s]])
+    g0, g1 = sharding.group_split(off, world)[rank]
+    a, b = int(off[g0]), int(off[g1])
+    sub = wl.Workload(p=w.p, n=w.n, coeffs=w.coeffs[a:b], exps=w.exps[a:b], beta=w.beta, T=w.T, t0=w.t0,
+                      name=w.name)
+    return sub, w.t0, int(w.T), "strong"
+
+
+def reduce_over_ranks(values, dist, device, op="max"):
+    """Element-wise max (or sum) of a list of floats over all ranks (identity
+    without a process group)."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(x) for x in t.cpu()]
 
 
 _HOST_CPU = None
@@ -674,10 +715,10 @@ def run_ours(args):
         variant = "fp64"
     if variant == "auto" and args.method == "matrix":    # an explicit product keeps poly_eval_run on the matrix method
         variant = "barrett32" if int(w.p) < (1 << 30) else "barrett64"
-    from paper_2004_11571_gb300 import sharding
-    t0, _ = sharding.weak_block(int(w.T), w.t0, rank)   # each rank: its own block of T points
+    w_full = w
+    w, t0, T, scaling = rank_share(w_full, args.split, rank, world)
     poly = pe.Poly.from_workload(w, variant=variant)
-    G, T, s = poly.G, int(w.T), w.s
+    G, s = poly.G, w.s
     tuned = None
     if args.tiles:
         K, slabs, tchunk, wpb, tail = (int(x) for x in args.tiles.split(","))
@@ -710,11 +751,10 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
     t_pt, t_a, t_b, runs = poly.kernel_times()
-    tot = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    max_total_ms = float(tot.item())
-    value = s * T * world * args.steps / (max_total_ms * 1e-3)
+    # Whole-job throughput: the term-points of every rank over the slowest rank's time.
+    max_total_ms, = reduce_over_ranks([total_ms], dist, "cuda", "max")
+    job_tp, = reduce_over_ranks([float(s) * T * args.steps], dist, "cuda", "sum")
+    value = job_tp / (max_total_ms * 1e-3)
     plan = poly.plan_info(T)
     launches = poly.launches_per_run(T) * args.steps
     fast_off = None
@@ -733,7 +773,8 @@ def run_ours(args):
         (p2.run_fast if args.method == "fast" else p2.run)(w.beta, T, t0, out=host_out)
         p2.close()
         e2e_t.append(time.perf_counter() - t_start)
-    e2e_val = s * T / statistics.median(e2e_t)
+    e2e_slowest, = reduce_over_ranks([statistics.median(e2e_t)], dist, "cuda", "max")
+    e2e_val = job_tp / args.steps / e2e_slowest
 
     if rank != 0:
         if dist is not None:
@@ -764,10 +805,11 @@ def run_ours(args):
                               stepb_traffic(args.config, vkey, plan))
     line = {"metric": "term-point evaluations/s", "value": value, "unit": "term-points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "higher_is_better": True, "scaling": scaling, "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": workload_config(w, args.config, variant, {"groups": G, "tiles": plan, "tuned": tuned is not None,
-                                                               "per_rank_points": f"t0 + rank*{T}"}),
+            "config": workload_config(w_full, args.config, variant,
+                                      {"groups": G, "tiles": plan, "tuned": tuned is not None, "split": args.split,
+                                       "rank0_points": f"{t0}..{t0 + T - 1}", "rank0_terms": s}),
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": "term-points/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(T * G * 8), "median_s": statistics.median(e2e_t)},
