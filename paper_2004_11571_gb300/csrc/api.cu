@@ -454,11 +454,13 @@ Tiles choose_tiles(pe_poly *P, uint64_t T, const pe_tiles *f)
     return t;
 }
 
-void build_chunks(pe_poly *P, uint32_t K)
+void build_gfirst(pe_poly *P, uint32_t K)
 {
     HostChunks &h = P->chunks;
-    if (h.K == K && !h.cs.empty()) return;
+    if (h.K == K && h.gfirst.size() == P->G + 1) return;
     h.K = K;
+    h.cs.clear();
+    h.cg.clear();
     h.gfirst.resize(P->G + 1);
     uint64_t nc = 0;
     for (uint64_t g = 0; g < P->G; ++g) {
@@ -466,6 +468,15 @@ void build_chunks(pe_poly *P, uint32_t K)
         nc += (P->group_off[g + 1] - P->group_off[g] + K - 1) / K;
     }
     h.gfirst[P->G] = (uint32_t)nc;
+    h.NC = (uint32_t)nc;
+}
+
+void build_chunks(pe_poly *P, uint32_t K)
+{
+    build_gfirst(P, K);
+    HostChunks &h = P->chunks;
+    if (h.cs.size() == (size_t)h.NC + 1) return;
+    const uint64_t nc = h.NC;
     h.cs.resize(nc + 1);
     h.cg.resize(nc);
     uint32_t *cs = h.cs.data(), *cg = h.cg.data();
@@ -485,14 +496,14 @@ void build_chunks(pe_poly *P, uint32_t K)
 
 void build_plan_host(pe_poly *P, const Tiles &t, uint64_t T, PlanHost &ph)
 {
-    build_chunks(P, t.K);
+    build_gfirst(P, t.K);
     const HostChunks &h = P->chunks;
     ph.K = t.K;
     ph.kslabs = t.kslabs;
     ph.Tc = t.Tc;
     ph.wpb = t.wpb;
     ph.T = T;
-    ph.NC = (uint32_t)h.cg.size();
+    ph.NC = h.NC;
     const uint32_t per_unit = 32u * t.kslabs;
     ph.U = (ph.NC + per_unit - 1) / per_unit;
     ph.Q = (uint32_t)((T + t.Tc - 1) / t.Tc);
@@ -577,31 +588,31 @@ pe_status ensure_plan(pe_poly *P, Plan &pl, const Tiles &t, uint64_t T, cudaStre
     build_plan_host(P, t, T, ph);
     const HostChunks &h = P->chunks;
     cudaError_t e;
-    auto alloc = [&](DevBuf &b, size_t n) { return queued ? b.ensure_async(n, st) : b.ensure(n); };
-    if ((e = alloc(pl.cs, h.cs.size() * 4)) != cudaSuccess || (e = alloc(pl.cg, std::max<size_t>(h.cg.size(), 1) * 4)) != cudaSuccess ||
+    // Synchronous plans are built on the library stream and waited for.
+    cudaStream_t ks = queued ? st : alloc_stream();
+    auto alloc = [&](DevBuf &b, size_t n) { return b.ensure_async(n, ks); };
+    if ((e = alloc(pl.cs, ((size_t)ph.NC + 1) * 4)) != cudaSuccess || (e = alloc(pl.cg, std::max<size_t>(ph.NC, 1) * 4)) != cudaSuccess ||
+        (e = alloc(pl.gfirst, h.gfirst.size() * 4)) != cudaSuccess ||
         (e = alloc(pl.unit, ph.unit.size() * 4)) != cudaSuccess || (e = alloc(pl.span, ph.span.size() * 4)) != cudaSuccess ||
         (e = alloc(pl.counters, ph.counter_bytes())) != cudaSuccess)
         return cuda_fail(e, "plan alloc");
     if ((e = alloc(pl.carry, ph.carry_bytes())) != cudaSuccess) return cuda_fail(e, "carry alloc");
     if ((e = alloc(pl.chain, ph.chain_bytes())) != cudaSuccess) return cuda_fail(e, "chain alloc");
-    if (queued) {
-        // Pageable sources are staged by the driver before these calls return.
-        if ((e = cudaMemcpyAsync(pl.cs.p, h.cs.data(), h.cs.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (ph.NC && (e = cudaMemcpyAsync(pl.cg.p, h.cg.data(), h.cg.size() * 4, cudaMemcpyHostToDevice, st)) !=
-                          cudaSuccess) ||
-            (e = cudaMemcpyAsync(pl.unit.p, ph.unit.data(), ph.unit.size() * 4, cudaMemcpyHostToDevice, st)) !=
-                cudaSuccess ||
-            (e = cudaMemcpyAsync(pl.span.p, ph.span.data(), ph.span.size() * 4, cudaMemcpyHostToDevice, st)) !=
-                cudaSuccess ||
-            (e = cudaMemsetAsync(pl.counters.p, 0, pl.counters.bytes, st)) != cudaSuccess)
-            return cuda_fail(e, "plan upload");
-    } else if ((e = cudaMemcpy(pl.cs.p, h.cs.data(), h.cs.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-               (ph.NC && (e = cudaMemcpy(pl.cg.p, h.cg.data(), h.cg.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) ||
-               (e = cudaMemcpy(pl.unit.p, ph.unit.data(), ph.unit.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-               (e = cudaMemcpy(pl.span.p, ph.span.data(), ph.span.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-               (e = cudaMemset(pl.counters.p, 0, pl.counters.bytes)) != cudaSuccess) {
-        return cuda_fail(e, "plan upload");
+    if (!P->goff_dev.p) {   // the group offsets, once per handle
+        std::vector<uint32_t> go(P->group_off.begin(), P->group_off.end());
+        if ((e = P->goff_dev.ensure_async(go.size() * 4, ks)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(P->goff_dev.p, go.data(), go.size() * 4, cudaMemcpyHostToDevice, ks)) != cudaSuccess)
+            return cuda_fail(e, "group offsets");
     }
+    // Pageable sources are staged by the driver before these calls return.
+    if ((e = cudaMemcpyAsync(pl.gfirst.p, h.gfirst.data(), h.gfirst.size() * 4, cudaMemcpyHostToDevice, ks)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(pl.unit.p, ph.unit.data(), ph.unit.size() * 4, cudaMemcpyHostToDevice, ks)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(pl.span.p, ph.span.data(), ph.span.size() * 4, cudaMemcpyHostToDevice, ks)) != cudaSuccess ||
+        (e = cudaMemsetAsync(pl.counters.p, 0, pl.counters.bytes, ks)) != cudaSuccess ||
+        (e = launch_chunk_tables(P->goff_dev.as<uint32_t>(), pl.gfirst.as<uint32_t>(), P->G, ph.K, P->s, ph.NC,
+                                 pl.cs.as<uint32_t>(), pl.cg.as<uint32_t>(), ks)) != cudaSuccess)
+        return cuda_fail(e, "plan upload");
+    if (!queued && (e = cudaStreamSynchronize(ks)) != cudaSuccess) return cuda_fail(e, "plan upload");
     pl.K = t.K;
     pl.kslabs = t.kslabs;
     pl.Tc = t.Tc;
@@ -693,7 +704,22 @@ static pe_status create_poly_device(const pe_poly_desc *d, int variant, pe_poly 
         return cuda_fail(e, "device allocation");
     }
     const void *dexps = d->exps;
-    if (!dev_in) {
+    auto page_locked = [](const void *p) {
+        cudaPointerAttributes a{};
+        const bool yes = cudaPointerGetAttributes(&a, p) == cudaSuccess && a.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        return yes;
+    };
+    if (!dev_in && page_locked(d->coeffs) && page_locked(d->exps)) {
+        // Page-locked caller arrays are read by the copy engine directly (the
+        // caller keeps them unchanged until create returns, which waits for it).
+        if ((e = cudaMemcpyAsync(P->coeffs.p, d->coeffs, cbytes, cudaMemcpyHostToDevice, us)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(raw.p, d->exps, ebytes, cudaMemcpyHostToDevice, us)) != cudaSuccess) {
+            finish();
+            return cuda_fail(e, "uploading terms");
+        }
+        dexps = raw.p;
+    } else if (!dev_in) {
         stg = stage_acquire(cbytes + ebytes);
         if (!stg.p) {
             finish();
@@ -1385,18 +1411,26 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
 constexpr uint64_t kPipelinedDownloadBytes = 16ull << 20;
 
 // Step B into host memory: one launch per T-chunk (main band, then tail
-// band), alternating between the run's stream and the handle's second stream,
-// each followed by the download of the rows it wrote.  Items of a later chunk
-// fill the SMs as an earlier chunk's items finish (launches on two streams
-// overlap), and each chunk's copy runs while the later chunks compute, so most
-// of the download is hidden.  T-chunks share nothing but read-only plan
-// tables: carries and arrival counters are per T-chunk, chain buffers per item.
+// band), alternating between the run's stream and the handle's second stream;
+// each chunk's rows are downloaded on a third stream as soon as that chunk's
+// launch has finished.  Items of a later chunk fill the SMs as an earlier
+// chunk's items finish (launches on two streams overlap), the copies never hold
+// up a launch, and only the last chunks' copies remain after the compute.
+// T-chunks share nothing but read-only plan tables: carries and arrival
+// counters are per T-chunk, chain buffers per item.
 static pe_status stepb_download_pipelined(pe_poly *P, const Tiles &t, StepBJob J0, StepBJob J1, uint64_t T0,
                                           uint64_t T, uint64_t *out, uint64_t *out_dev, cudaStream_t cs)
 {
     cudaError_t e;
-    if (!P->aux && (e = cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking)) != cudaSuccess)
-        return cuda_fail(e, "second stream");
+    if ((!P->aux && (e = cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking)) != cudaSuccess) ||
+        (!P->copy_st && (e = cudaStreamCreateWithFlags(&P->copy_st, cudaStreamNonBlocking)) != cudaSuccess))
+        return cuda_fail(e, "streams");
+    const uint32_t nchunks = P->plan.Q + (T > T0 ? P->tail_plan.Q : 0);
+    while (P->chunk_ev.size() < nchunks) {
+        cudaEvent_t x;
+        if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "events");
+        P->chunk_ev.push_back(x);
+    }
     if ((!P->fork_ev && (e = cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming)) != cudaSuccess) ||
         (!P->join_ev && (e = cudaEventCreateWithFlags(&P->join_ev, cudaEventDisableTiming)) != cudaSuccess))
         return cuda_fail(e, "events");
@@ -1416,12 +1450,16 @@ static pe_status stepb_download_pipelined(pe_poly *P, const Tiles &t, StepBJob J
             if ((e = launch_stepB((int)t.K, P->variant, J, pl.U, none, 0, (int)t.wpb, st)) != cudaSuccess)
                 return cuda_fail(e, "Step B");
             const uint64_t r0 = row0 + (uint64_t)q * pl.Tc, r1 = std::min<uint64_t>(row0 + rows, r0 + pl.Tc);
-            if ((e = cudaMemcpyAsync(out + r0 * G, out_dev + r0 * G, (r1 - r0) * G * 8, cudaMemcpyDeviceToHost, st)) !=
-                cudaSuccess)
+            if ((e = cudaEventRecord(P->chunk_ev[k], st)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(P->copy_st, P->chunk_ev[k], 0)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(out + r0 * G, out_dev + r0 * G, (r1 - r0) * G * 8, cudaMemcpyDeviceToHost,
+                                     P->copy_st)) != cudaSuccess)
                 return cuda_fail(e, "copy back");
         }
     }
-    if ((e = cudaEventRecord(P->join_ev, P->aux)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, P->join_ev, 0)) != cudaSuccess)
+    // The copy stream waited for every chunk, so joining it covers both launch streams.
+    if ((e = cudaEventRecord(P->join_ev, P->copy_st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(cs, P->join_ev, 0)) != cudaSuccess)
         return cuda_fail(e, "join");
     return PE_OK;
 }

@@ -240,6 +240,7 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
         if (!queued(j)) continue;
         const Tiles t = batch_tiles(P, jobs[j].T, w_target);
         build_plan_host(P, t, jobs[j].T, ph[j]);
+        build_chunks(P, t.K);                  // the image holds the chunk tables
         cs[j] = P->chunks.cs;
         cg[j] = P->chunks.cg;
         var[j] = resolve_variant(P, jobs[j].T);

@@ -104,14 +104,19 @@ struct Plan {
     uint32_t K = 0, kslabs = 0, Q = 0, Tc = 0, wpb = 0;
     uint64_t T = 0;
     uint32_t NC = 0, U = 0, S = 0, nslots = 0;
-    DevBuf cs, cg, unit, span, counters, carry, chain;
+    DevBuf cs, cg, gfirst, unit, span, counters, carry, chain;
     uint64_t scratch_bytes() const { return counters.bytes + carry.bytes + chain.bytes; }
 };
 
+// Lane chunks of at most K terms of one group.  gfirst (the first chunk of
+// each group, G+1 entries) is always on the host; the per-chunk arrays cs/cg
+// are built on the host only where a batch copies them into its image (a
+// plain run builds them on the device from gfirst and the group offsets).
 struct HostChunks {
     uint32_t K = 0;
-    std::vector<uint32_t> cs, cg;       // NC+1, NC
+    uint32_t NC = 0;
     std::vector<uint32_t> gfirst;       // first chunk of each group, G+1
+    std::vector<uint32_t> cs, cg;       // NC+1, NC (empty until build_chunks)
 };
 
 struct Tiles {
@@ -182,6 +187,7 @@ struct pe_poly {
     std::vector<uint64_t> group_off;   // G+1 (host)
     std::vector<uint32_t> keys;        // 2G (host)
     pe::DevBuf coeffs, mR, ptab, out_scratch, vstart;
+    pe::DevBuf goff_dev;                // G+1 uint32 group offsets on the device (plain-run chunk tables)
     // Exponents of x3..xn (E rows of s), shared with the polynomials made by
     // poly_eval_create_like, and the permutation that put the input terms in
     // group order (empty when they already were).
@@ -197,23 +203,28 @@ struct pe_poly {
     std::vector<cudaEvent_t> events;   // 4 per timed run
     size_t events_used = 0;
     cudaEvent_t last_use = nullptr;    // end of the latest run; frees of this handle's buffers wait for it
-    // Second stream of a run into host memory (T-chunks alternate between the
-    // run's stream and this one), with its fork and join events.
-    cudaStream_t aux = nullptr;
+    // A run into page-locked host memory: T-chunks alternate between the run's
+    // stream and `aux`; their downloads queue on `copy_st`, each after its
+    // chunk's event; fork and join events tie them to the run's stream.
+    cudaStream_t aux = nullptr, copy_st = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    std::vector<cudaEvent_t> chunk_ev;
     ~pe_poly()
     {
         for (cudaEvent_t e : events) cudaEventDestroy(e);
+        for (cudaEvent_t e : chunk_ev) cudaEventDestroy(e);
         if (last_use) cudaEventDestroy(last_use);
         if (fork_ev) cudaEventDestroy(fork_ev);
         if (join_ev) cudaEventDestroy(join_ev);
         if (aux) cudaStreamDestroy(aux);
+        if (copy_st) cudaStreamDestroy(copy_st);
     }
     uint64_t device_bytes() const
     {
-        return coeffs.bytes + (exps.use_count() == 1 ? exps->bytes : 0) + mR.bytes + ptab.bytes + out_scratch.bytes + vstart.bytes + plan.cs.bytes +
-               plan.cg.bytes + plan.unit.bytes + plan.span.bytes + plan.scratch_bytes() + tail_plan.cs.bytes +
-               tail_plan.cg.bytes + tail_plan.unit.bytes + tail_plan.span.bytes + tail_plan.scratch_bytes();
+        return coeffs.bytes + (exps.use_count() == 1 ? exps->bytes : 0) + mR.bytes + ptab.bytes + out_scratch.bytes + vstart.bytes +
+               goff_dev.bytes + plan.cs.bytes + plan.cg.bytes + plan.gfirst.bytes + plan.unit.bytes + plan.span.bytes +
+               plan.scratch_bytes() + tail_plan.cs.bytes + tail_plan.cg.bytes + tail_plan.gfirst.bytes +
+               tail_plan.unit.bytes + tail_plan.span.bytes + tail_plan.scratch_bytes();
     }
 };
 
@@ -239,6 +250,7 @@ Tiles choose_tiles(pe_poly *poly, uint64_t T, const pe_tiles *forced);
 // otherwise they complete before the call returns.
 pe_status ensure_plan(pe_poly *poly, Plan &pl, const Tiles &t, uint64_t T, cudaStream_t st = nullptr,
                       bool queued = false);
+void build_gfirst(pe_poly *P, uint32_t K);
 void build_chunks(pe_poly *P, uint32_t K);
 void build_plan_host(pe_poly *P, const Tiles &t, uint64_t T, PlanHost &ph);
 void fill_job(StepBJob &J, pe_poly *P, const PlanHost &ph, const uint32_t *cs, const uint32_t *cg,

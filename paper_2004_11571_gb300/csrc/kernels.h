@@ -14,6 +14,10 @@ cudaError_t launch_stepA(const void *exps, uint32_t exp_bytes, uint64_t s, uint3
 cudaError_t launch_stepA_starts(const void *exps, uint32_t exp_bytes, const uint64_t *coeffs, uint64_t s, uint32_t E,
                                const uint64_t *ptab, uint32_t dp1, const ModCtx &mc, uint64_t t0, const StartRows &sr,
                                uint64_t *mR, uint64_t *vstart, int num_sms, cudaStream_t st);
+// Chunk tables of a plan (cs: NC+1 chunk starts, cg: NC group ids) from the
+// group offsets and each group's first chunk.
+cudaError_t launch_chunk_tables(const uint32_t *goff, const uint32_t *gfirst, uint64_t G, uint32_t K, uint64_t s,
+                                uint32_t NC, uint32_t *cs, uint32_t *cg, cudaStream_t st);
 cudaError_t launch_stepB(int K, int var, const StepBJob &J0, uint32_t n0, const StepBJob &J1, uint32_t n1, int wpb,
                          cudaStream_t st);
 cudaError_t stepB_occupancy(int K, int var, int wpb, int *blocks_per_sm);

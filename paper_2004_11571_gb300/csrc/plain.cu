@@ -1,4 +1,5 @@
 // Plain (one polynomial per call) kernels: power tables, Step A, Step B.
+#include <algorithm>
 #include <cstdio>
 #include "common.h"
 #include "modarith.cuh"
@@ -63,6 +64,37 @@ __global__ void k_stepA_starts(const ExpT *__restrict__ exps, const uint64_t *__
             vstart[(uint64_t)k * s + i] = cur;
         }
     }
+}
+
+// ------------------------------------------------------------ chunk tables
+// Lane chunks of a plan: chunk c belongs to the group g with
+// gfirst[g] <= c < gfirst[g+1] and starts at term goff[g] + (c - gfirst[g]) K.
+__global__ void k_chunk_tables(const uint32_t *__restrict__ goff, const uint32_t *__restrict__ gfirst, uint32_t G,
+                               uint32_t K, uint32_t s, uint32_t NC, uint32_t *__restrict__ cs, uint32_t *__restrict__ cg)
+{
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c <= NC; c += gridDim.x * blockDim.x) {
+        if (c == NC) {
+            cs[NC] = s;
+            continue;
+        }
+        uint32_t lo = 0, hi = G;   // largest g with gfirst[g] <= c
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (gfirst[mid] <= c) lo = mid;
+            else hi = mid;
+        }
+        cs[c] = goff[lo] + (c - gfirst[lo]) * K;
+        cg[c] = lo;
+    }
+}
+
+cudaError_t launch_chunk_tables(const uint32_t *goff, const uint32_t *gfirst, uint64_t G, uint32_t K, uint64_t s,
+                                uint32_t NC, uint32_t *cs, uint32_t *cg, cudaStream_t st)
+{
+    if (G == 0) return cudaSuccess;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(((uint64_t)NC + 256) / 256, 4096);
+    k_chunk_tables<<<grid, 256, 0, st>>>(goff, gfirst, (uint32_t)G, K, (uint32_t)s, NC, cs, cg);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------- Step B

@@ -94,3 +94,21 @@ def test_device_path_errors():
     poly = pe.Poly(w.p, w.coeffs, w.exps)
     _check(poly, w, keys_ref, ref)
     poly.close()
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_page_locked_host_input_is_read_directly(dtype):
+    # Terms in page-locked host memory are uploaded by the copy engine without
+    # a staging copy; the result must be the same polynomial, also for a
+    # coefficient that is not reduced (reported, not uploaded silently).
+    w = wl.make_zipf(n=7, s=50_000, p=P62, deg12=20, deg_rest=9, T=20, seed=8)
+    keys_ref, ref = oracle.eval_direct(w)
+    c = torch.from_numpy(w.coeffs.view(np.int64)).pin_memory().numpy().view(np.uint64)
+    e = torch.from_numpy(np.ascontiguousarray(w.exps.astype(dtype))).pin_memory().numpy()
+    poly = pe.Poly(w.p, c, e, sorted_hint=True)
+    _check(poly, w, keys_ref, ref)
+    poly.close()
+    c[1234] = np.uint64(w.p)
+    with pytest.raises(pe.PolyEvalError) as err:
+        pe.Poly(w.p, c, e)
+    assert err.value.status == pe.PE_ERR_NOT_REDUCED
