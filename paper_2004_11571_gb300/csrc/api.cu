@@ -673,6 +673,7 @@ static pe_status check_prime(uint64_t p, int variant)
 // *fallback, and does nothing else, when the terms are not in group order or
 // staging memory is unavailable; the host path then handles them.
 static constexpr uint64_t kDeviceCreateMin = 1u << 14;
+static constexpr uint64_t kEarlyGroups = 1u << 14;   // group-table entries fetched with the first wait
 
 static pe_status create_poly_device(const pe_poly_desc *d, int variant, pe_poly **out, bool host_threads,
                                     bool *fallback)
@@ -747,17 +748,41 @@ static pe_status create_poly_device(const pe_poly_desc *d, int variant, pe_poly 
     }
     CreateInfo ci{};
     uint64_t G = 0;
+    // With byte exponents the packed rows are bytes whatever the scan finds, so
+    // the packing and a bounded copy of the group table are queued before the
+    // first wait: a polynomial of at most kEarlyGroups groups needs one wait.
+    const bool early = w == 1 && E > 0;
+    const uint64_t early_groups = std::min<uint64_t>(s, kEarlyGroups);
+    Staging gst{};
+    if (early) {
+        gst = stage_acquire(early_groups * 16);
+        if ((e = P->exps->ensure_async((size_t)E * s, us)) != cudaSuccess) {
+            finish();
+            stage_release(gst);
+            return cuda_fail(e, "device allocation");
+        }
+    }
     if ((e = cudaMemsetAsync(info.p, 0, sizeof(CreateInfo), us)) != cudaSuccess ||
         (e = cudaMemsetAsync(info.p, 0xff, sizeof(unsigned long long), us)) != cudaSuccess ||
         (e = launch_term_scan(P->coeffs.as<uint64_t>(), dexps, w, s, n, d->p, keys.as<uint64_t>(),
                               info.as<CreateInfo>(), counts.as<uint64_t>(), base.as<uint64_t>(), goff.as<uint64_t>(),
                               gkeys.as<uint32_t>(), us)) != cudaSuccess ||
+        (early && (e = launch_pack_exps(dexps, 1, s, n, 1, P->exps->p, us)) != cudaSuccess) ||
+        (early && gst.p &&
+         ((e = cudaMemcpyAsync(gst.p, goff.p, early_groups * 8, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
+          (e = cudaMemcpyAsync((unsigned char *)gst.p + early_groups * 8, gkeys.p, early_groups * 8,
+                               cudaMemcpyDeviceToHost, us)) != cudaSuccess)) ||
         (e = cudaMemcpyAsync(&ci, info.p, sizeof ci, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
         (e = cudaMemcpyAsync(&G, base.as<uint64_t>() + nb, 8, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
         (e = cudaStreamSynchronize(us)) != cudaSuccess) {
         finish();
+        stage_release(gst);
         return cuda_fail(e, "scanning terms");
     }
+    struct StageGuard {
+        Staging &g;
+        ~StageGuard() { stage_release(g); }
+    } guard{gst};
     if (ci.bad != ~0ull) {
         uint64_t v = 0;
         if (dev_in)
@@ -791,12 +816,18 @@ static pe_status create_poly_device(const pe_poly_desc *d, int variant, pe_poly 
     P->group_off.resize(G + 1);
     P->keys.resize(2 * G);
     const size_t dp1 = ci.dmax + 1;
-    if ((e = P->exps->ensure_async((size_t)E * s * P->exp_bytes, us)) != cudaSuccess ||
-        (e = P->ptab.ensure_async((size_t)E * dp1 * 8, us)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(P->group_off.data(), goff.p, G * 8, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(P->keys.data(), gkeys.p, 2 * G * 4, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
-        (e = launch_pack_exps(dexps, w, s, n, P->exp_bytes, P->exps->p, us)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(us)) != cudaSuccess) {
+    if ((e = P->ptab.ensure_async((size_t)E * dp1 * 8, us)) != cudaSuccess) {
+        finish();
+        return cuda_fail(e, "device allocation");
+    }
+    if (early && gst.p && G <= early_groups) {   // everything arrived with the first wait
+        memcpy(P->group_off.data(), gst.p, G * 8);
+        memcpy(P->keys.data(), (const unsigned char *)gst.p + early_groups * 8, G * 8);
+    } else if ((!early && (e = P->exps->ensure_async((size_t)E * s * P->exp_bytes, us)) != cudaSuccess) ||
+               (e = cudaMemcpyAsync(P->group_off.data(), goff.p, G * 8, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
+               (e = cudaMemcpyAsync(P->keys.data(), gkeys.p, 2 * G * 4, cudaMemcpyDeviceToHost, us)) != cudaSuccess ||
+               (!early && (e = launch_pack_exps(dexps, w, s, n, P->exp_bytes, P->exps->p, us)) != cudaSuccess) ||
+               (e = cudaStreamSynchronize(us)) != cudaSuccess) {
         finish();
         return cuda_fail(e, "packing terms");
     }
@@ -1411,7 +1442,7 @@ extern "C" pe_status poly_eval_run(pe_poly *P, const uint64_t *beta, uint64_t T,
 constexpr uint64_t kPipelinedDownloadBytes = 16ull << 20;
 
 // Step B into host memory: one launch per T-chunk (main band, then tail
-// band), alternating between the run's stream and the handle's second stream;
+// band), rotating over the run's stream and two more of the handle's streams;
 // each chunk's rows are downloaded on a third stream as soon as that chunk's
 // launch has finished.  Items of a later chunk fill the SMs as an earlier
 // chunk's items finish (launches on two streams overlap), the copies never hold
@@ -1422,9 +1453,8 @@ static pe_status stepb_download_pipelined(pe_poly *P, const Tiles &t, StepBJob J
                                           uint64_t T, uint64_t *out, uint64_t *out_dev, cudaStream_t cs)
 {
     cudaError_t e;
-    if ((!P->aux && (e = cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking)) != cudaSuccess) ||
-        (!P->copy_st && (e = cudaStreamCreateWithFlags(&P->copy_st, cudaStreamNonBlocking)) != cudaSuccess))
-        return cuda_fail(e, "streams");
+    for (cudaStream_t *a : {&P->aux[0], &P->aux[1], &P->copy_st})
+        if (!*a && (e = cudaStreamCreateWithFlags(a, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "streams");
     const uint32_t nchunks = P->plan.Q + (T > T0 ? P->tail_plan.Q : 0);
     while (P->chunk_ev.size() < nchunks) {
         cudaEvent_t x;
@@ -1434,8 +1464,10 @@ static pe_status stepb_download_pipelined(pe_poly *P, const Tiles &t, StepBJob J
     if ((!P->fork_ev && (e = cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming)) != cudaSuccess) ||
         (!P->join_ev && (e = cudaEventCreateWithFlags(&P->join_ev, cudaEventDisableTiming)) != cudaSuccess))
         return cuda_fail(e, "events");
-    if ((e = cudaEventRecord(P->fork_ev, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(P->aux, P->fork_ev, 0)) != cudaSuccess)
+    if ((e = cudaEventRecord(P->fork_ev, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(P->aux[0], P->fork_ev, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(P->aux[1], P->fork_ev, 0)) != cudaSuccess)
         return cuda_fail(e, "fork");
+    const cudaStream_t launch_st[3] = {cs, P->aux[0], P->aux[1]};
     const uint64_t G = P->G;
     const StepBJob none{};
     uint32_t k = 0;
@@ -1445,7 +1477,9 @@ static pe_status stepb_download_pipelined(pe_poly *P, const Tiles &t, StepBJob J
         const uint64_t rows = band == 0 ? T0 : T - T0, row0 = band == 0 ? 0 : T0;
         if (!rows) continue;
         for (uint32_t q = 0; q < pl.Q; ++q, ++k) {
-            cudaStream_t st = (k & 1) ? P->aux : cs;
+            // Three launch streams: a chunk waits only for the chunk three
+            // before it, so the tail band's chunks start as SMs free up.
+            cudaStream_t st = launch_st[k % 3];
             J.item0 = q * pl.U;
             if ((e = launch_stepB((int)t.K, P->variant, J, pl.U, none, 0, (int)t.wpb, st)) != cudaSuccess)
                 return cuda_fail(e, "Step B");
@@ -1457,7 +1491,7 @@ static pe_status stepb_download_pipelined(pe_poly *P, const Tiles &t, StepBJob J
                 return cuda_fail(e, "copy back");
         }
     }
-    // The copy stream waited for every chunk, so joining it covers both launch streams.
+    // The copy stream waited for every chunk, so joining it covers every launch stream.
     if ((e = cudaEventRecord(P->join_ev, P->copy_st)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(cs, P->join_ev, 0)) != cudaSuccess)
         return cuda_fail(e, "join");

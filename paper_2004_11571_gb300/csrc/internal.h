@@ -203,10 +203,10 @@ struct pe_poly {
     std::vector<cudaEvent_t> events;   // 4 per timed run
     size_t events_used = 0;
     cudaEvent_t last_use = nullptr;    // end of the latest run; frees of this handle's buffers wait for it
-    // A run into page-locked host memory: T-chunks alternate between the run's
-    // stream and `aux`; their downloads queue on `copy_st`, each after its
-    // chunk's event; fork and join events tie them to the run's stream.
-    cudaStream_t aux = nullptr, copy_st = nullptr;
+    // A run into page-locked host memory: T-chunks rotate over the run's
+    // stream and `aux[0..1]`; their downloads queue on `copy_st`, each after
+    // its chunk's event; fork and join events tie them to the run's stream.
+    cudaStream_t aux[2] = {nullptr, nullptr}, copy_st = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     std::vector<cudaEvent_t> chunk_ev;
     ~pe_poly()
@@ -216,7 +216,8 @@ struct pe_poly {
         if (last_use) cudaEventDestroy(last_use);
         if (fork_ev) cudaEventDestroy(fork_ev);
         if (join_ev) cudaEventDestroy(join_ev);
-        if (aux) cudaStreamDestroy(aux);
+        for (cudaStream_t a : aux)
+            if (a) cudaStreamDestroy(a);
         if (copy_st) cudaStreamDestroy(copy_st);
     }
     uint64_t device_bytes() const
