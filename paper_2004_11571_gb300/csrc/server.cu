@@ -63,6 +63,7 @@ struct Slot {
     std::vector<SrvRequest *> reqs;
     bool busy = false;
     double term_points = 0.0;
+    uint64_t device_bytes = 0;        // arena + outs, published under the server mutex
 };
 
 static uint64_t poly_bytes_estimate(const pe_poly_desc &d)
@@ -107,14 +108,14 @@ struct pe_server {
     uint64_t slot_bytes() const
     {
         uint64_t b = 0;
-        for (uint32_t i = 0; i < nslots; ++i) b += slots[i].arena.bytes + slots[i].outs.bytes;
+        for (uint32_t i = 0; i < nslots; ++i) b += slots[i].device_bytes;
         return b;
     }
 
     uint64_t committed() const
     {
         uint64_t b = resident_bytes + reserved_bytes;
-        for (uint32_t i = 0; i < nslots; ++i) b += slots[i].arena.bytes + slots[i].outs.bytes;
+        for (uint32_t i = 0; i < nslots; ++i) b += slots[i].device_bytes;
         return b;
     }
 
@@ -335,6 +336,7 @@ struct pe_server {
         s.busy = true;
         t_launch += since(t_la0);
         std::lock_guard<std::mutex> lk(mu);
+        s.device_bytes = s.arena.bytes + s.outs.bytes;   // the epoch thread alone resizes them
         if (inflight++ == 0) busy_since = Clock::now();
         ++epochs;
         return true;
@@ -363,6 +365,7 @@ struct pe_server {
                     if (!slots[i].busy) {
                         slots[i].arena.release();
                         slots[i].outs.release();
+                        slots[i].device_bytes = 0;
                     }
                 cv_upload.notify_all();
             }

@@ -228,7 +228,9 @@ __device__ __forceinline__ void stepb_item(const StepBJob &J, uint32_t item, War
                 uint32_t hi;
                 lane_point<K, VAR>(st, mc, lo, hi);
                 sm.lo[tt * kWalkStride + lane] = lo;
-                sm.hi[tt * kWalkStride + lane] = (uint8_t)hi;
+                // The 32-bit product's sums never reach 2^64 (values below
+                // 2^31, fewer than 2^32 terms): its high word is always zero.
+                if constexpr (VAR != VAR_BARRETT32) sm.hi[tt * kWalkStride + lane] = (uint8_t)hi;
             }
             __syncwarp();
             if ((uint32_t)lane < nt) {
@@ -245,7 +247,10 @@ __device__ __forceinline__ void stepb_item(const StepBJob &J, uint32_t item, War
                         ahi = 0;
                         first = false;
                     }
-                    add96(alo, ahi, plo[l], phi[l]);
+                    if constexpr (VAR == VAR_BARRETT32)
+                        alo += plo[l];
+                    else
+                        add96(alo, ahi, plo[l], phi[l]);
                 }
                 if (chain_out)
                     chain[row - r_begin] = make_ulonglong2(alo, ahi);
