@@ -107,6 +107,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=0.0,
                     help="Poisson request rate; 0 = 0.7x the burst capacity measured in the same run")
     ap.add_argument("--serve-burst", type=int, default=1500)
+    ap.add_argument("--serve-streams", type=int, default=4, help="epochs in flight at once (at most 4)")
+    ap.add_argument("--serve-epoch-jobs", type=int, default=64, help="requests per epoch at most")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
     ap.add_argument("--no-tune", action="store_true", help="skip poly_eval_tune before timing")
     ap.add_argument("--variant", default="auto")
@@ -1098,10 +1100,10 @@ def run_served(args, pool=None):
     burst = wl.served_requests(seed=wl.SEED_SERVE, rate=2000.0, duration=1.0 + args.serve_burst / 2000.0,
                                pool=pool)[:args.serve_burst]
     # (1) burst: throughput at saturation
-    srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
+    srv = pe.Server(mem_cap_bytes=40 << 30, streams=args.serve_streams, max_epoch_jobs=args.serve_epoch_jobs)
     drive(burst[:50], srv, False)                      # warm-up
     srv.close()
-    srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
+    srv = pe.Server(mem_cap_bytes=40 << 30, streams=args.serve_streams, max_epoch_jobs=args.serve_epoch_jobs)
     t_burst, tp_burst, chk_burst = drive(burst, srv, False)
     st_burst = srv.stats()
     srv.close()
@@ -1125,7 +1127,7 @@ def run_served(args, pool=None):
     capacity = len(burst) / t_burst
     rate = args.serve_rate if args.serve_rate > 0 else 0.7 * capacity
     reqs = wl.served_requests(seed=wl.SEED_SERVE, rate=rate, duration=args.serve_seconds, pool=pool)
-    srv = pe.Server(mem_cap_bytes=40 << 30, streams=2, max_epoch_jobs=64)
+    srv = pe.Server(mem_cap_bytes=40 << 30, streams=args.serve_streams, max_epoch_jobs=args.serve_epoch_jobs)
     submit_s[0] = 0.0
     t_pois, tp_pois, chk_pois = drive(reqs, srv, True)
     st_pois = srv.stats()

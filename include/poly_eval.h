@@ -395,13 +395,13 @@ pe_status poly_eval_tune_load(const char *path);
  * Server: continuous batching of evaluation requests.  Requests are
  * admitted by device memory, polynomials can stay resident across
  * requests, and admitted jobs are packed into persistent-kernel epochs
- * that overlap on two streams.
+ * that overlap on up to four streams (four by default).
  * ---------------------------------------------------------------------- */
 typedef struct {
     uint64_t mem_cap_bytes;   /* cap on resident terms + scratch + outputs */
     uint32_t max_queue;       /* pending requests before PE_ERR_ADMISSION */
     uint32_t max_epoch_jobs;  /* jobs packed into one epoch */
-    uint32_t streams;         /* epochs in flight (1..4) */
+    uint32_t streams;         /* epochs in flight (1..4; 0: 4) */
 } pe_server_cfg;
 
 typedef struct pe_server pe_server;

@@ -385,7 +385,7 @@ class Server:
     (T x G uint64; page-locked buffers take the asynchronous path)."""
 
     def __init__(self, mem_cap_bytes: int = 40 << 30, max_queue: int = 4096, max_epoch_jobs: int = 256,
-                 streams: int = 2):
+                 streams: int = 4):
         cfg = _ServerCfg(int(mem_cap_bytes), int(max_queue), int(max_epoch_jobs), int(streams))
         h = ctypes.c_void_p()
         _check(lib().poly_eval_server_create(ctypes.byref(cfg), ctypes.byref(h)))

@@ -138,7 +138,7 @@ def test_served_stream_sample_every_cell(cap_gb):
     want = dict(zip([r["index"] for r in sample], _expected_many(sample, [ws[r["index"]] for r in sample])))
     G = [int(len(np.unique(w.exps[:, 0].astype(np.int64) * 65536 + w.exps[:, 1]))) for w in pool]
     ring = torch.empty(2 << 30, dtype=torch.uint8, pin_memory=True).numpy()
-    srv = pe.Server(mem_cap_bytes=cap_gb << 30, streams=2, max_epoch_jobs=64)
+    srv = pe.Server(mem_cap_bytes=cap_gb << 30, max_epoch_jobs=64)
     inflight, head, ids, got, checked = [], 0, {}, {}, 0
 
     def retire():

@@ -265,3 +265,22 @@ def test_device_pointer_input_and_u32_exponents():
     poly = pe.Poly(w.p, w.coeffs, w.exps.astype(np.uint32))          # host, 4-byte exponents
     assert np.array_equal(pe.to_u64(poly.run(w.beta, w.T)), ref)
     poly.close()
+
+
+@pytest.mark.parametrize("tiles", [None, dict(K=8, slabs=1, tchunk=32, warps_per_block=4)])
+def test_pinned_host_output_downloaded_by_chunk(tiles):
+    # Outputs of at least 16 MB into page-locked host memory are computed and
+    # downloaded T-chunk by T-chunk on several streams: every cell must still
+    # equal the oracle's, with the default tiles (no tail band at T = 448) and
+    # with 14 chunks of 32 points rotating over all three launch streams.
+    w = wl.make_zipf(n=7, s=200_000, p=P62, deg12=70, deg_rest=9, T=448, seed=51)
+    keys_ref, ref = oracle.eval_direct(w, t0=3)
+    poly = pe.Poly.from_workload(w)
+    if tiles:
+        poly.set_tiles(**tiles)
+    assert np.array_equal(poly.groups(), keys_ref) and ref.nbytes >= 16 << 20
+    for _ in range(2):
+        out = torch.full((w.T, poly.G), -1, dtype=torch.int64, pin_memory=True)
+        poly.run(w.beta, w.T, 3, out=out.numpy())
+        assert np.array_equal(out.numpy().view(np.uint64), ref)
+    poly.close()
