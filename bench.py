@@ -108,7 +108,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-rate", type=float, default=0.0,
                     help="Poisson request rate; 0 = 0.7x the burst capacity measured in the same run")
-    ap.add_argument("--serve-burst", type=int, default=1500)
+    ap.add_argument("--serve-burst", type=int, default=3000)
     ap.add_argument("--serve-streams", type=int, default=4, help="epochs in flight at once (at most 4)")
     ap.add_argument("--serve-epoch-jobs", type=int, default=64, help="requests per epoch at most")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
