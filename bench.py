@@ -152,13 +152,13 @@ def make_workload(name, terms=0, points=0):
     return wl.config_width(50, **kw)
 
 
-def workload_config(w, name, variant, extra=None):
-    cfg = {"workload": w.name, "terms": w.s, "n": w.n, "T": int(w.T), "prime_bits": int(w.p).bit_length(),
-           "variant": variant, "config": name,
-           "l2": "flushed between timed steps by a 256 MB device write"}
-    if extra:
-        cfg.update(extra)
-    return cfg
+def workload_config(w, name):
+    """The workload as both arms name it (the same dict for the GPU arm and the
+    oracle's reference arm); how an arm ran it goes under its own keys."""
+    key = w.exps[:, 0].astype(np.int64) * (1 << 32) + w.exps[:, 1].astype(np.int64)
+    return {"workload": w.name, "terms": w.s, "n": w.n, "T": int(w.T), "prime_bits": int(w.p).bit_length(),
+            "groups": int(np.unique(key).shape[0]), "config": name,
+            "l2": "GPU arm: flushed between timed steps by a 256 MB device write"}
 
 
 class ClockSampler:
@@ -697,7 +697,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": workload_config(w, args.config, "oracle"),
+            "config": workload_config(w, args.config),
+            "plan": {"implementation": "the oracle's matrix method (gcc -O2), one host core"},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": value,
                              "unit": "term-points/s", "host": host_cpu()},
             "e2e": {"value": value, "unit": "term-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -823,9 +824,9 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
             "higher_is_better": True, "scaling": scaling, "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": workload_config(w_full, args.config, variant,
-                                      {"groups": G, "tiles": plan, "tuned": tuned is not None, "split": args.split,
-                                       "rank0_points": f"{t0}..{t0 + T - 1}", "rank0_terms": s}),
+            "config": workload_config(w_full, args.config),
+            "plan": {"variant": variant, "tiles": plan, "tuned": tuned is not None, "split": args.split,
+                     "rank0_points": f"{t0}..{t0 + T - 1}", "rank0_terms": s, "rank0_groups": G},
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": "term-points/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(T * G * 8), "median_s": statistics.median(e2e_t)},

@@ -23,6 +23,10 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["host"]["model"] and d["cpu_baseline"]["host"]["logical_cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["terms"] == 2000 and d["config"]["T"] == 64
+    sys.path.insert(0, ROOT)
+    import bench
+    # the GPU arm names the workload with the same dict (its own run details go under "plan")
+    assert d["config"] == bench.workload_config(bench.make_workload("tiny"), "tiny")
 
 
 def test_reference_arm_other_ranks_exit_quietly():
