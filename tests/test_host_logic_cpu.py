@@ -86,12 +86,14 @@ def test_vdm_counts():
     assert corr == 0 + 1 + 10 and horner == 2 * (1 + 4 + 25) and n2 == 30
 
 
-def test_traffic_reported_only_for_the_captured_shape():
-    shape = dict(bench.STEPB_TRAFFIC_LARGE["shape"])
-    assert bench.stepb_traffic("large", "barrett64", shape) == bench.STEPB_TRAFFIC_LARGE["bytes"]
-    other = dict(shape, K=8)
-    assert bench.stepb_traffic("large", "barrett64", other) is None
-    assert bench.stepb_traffic("width62", "barrett64", shape) is None
+def test_traffic_reported_only_for_a_captured_shape():
+    assert len(bench.STEPB_TRAFFIC_LARGE) >= 2
+    for ref in bench.STEPB_TRAFFIC_LARGE:
+        shape = dict(ref["shape"], variant=3, chunks=1)          # extra plan keys do not matter
+        assert bench.stepb_traffic("large", "barrett64", shape) == ref["bytes"]
+        assert bench.stepb_traffic("large", "barrett64", dict(shape, K=8)) is None
+        assert bench.stepb_traffic("large", "mont64", shape) is None
+        assert bench.stepb_traffic("width62", "barrett64", shape) is None
 
 
 def test_cpu_baseline_sample_covers_disjoint_groups():
