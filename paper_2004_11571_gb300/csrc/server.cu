@@ -72,6 +72,12 @@ static uint64_t poly_bytes_estimate(const pe_poly_desc &d)
     return d.s * (8 + 8 + E * 2) + 4096;
 }
 
+// Epoch hold (see pe_server::launch).  Measured on the served mixture: paced
+// streams ran with about half the p50 and a lower p99 at the same or higher
+// rate, and bursts were no slower.
+constexpr size_t kHoldJobs = 16;
+constexpr double kHoldSeconds = 0.002;
+
 static double since(Clock::time_point a) { return std::chrono::duration<double>(Clock::now() - a).count(); }
 
 }  // namespace pe
@@ -267,6 +273,12 @@ struct pe_server {
         {
             std::lock_guard<std::mutex> lk(mu);
             uint64_t need = 0;
+            // While other epochs run, a small epoch waits briefly for more
+            // requests: larger epochs use the GPU better, and the wait ends as
+            // soon as kHoldJobs are ready or the oldest has waited kHoldSeconds.
+            if (!stop && inflight > 0 && !ready.empty() && ready.size() < kHoldJobs &&
+                std::chrono::duration<double>(Clock::now() - ready.front()->submitted).count() < kHoldSeconds)
+                return false;
             while (!paused && !ready.empty() && ok.size() < cfg.max_epoch_jobs) {
                 SrvRequest *r = ready.front();
                 const uint64_t add = r->T * r->poly->G * 8 + r->poly->s * 24 + r->T * 1024;
