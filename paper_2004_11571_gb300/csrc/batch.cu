@@ -281,13 +281,20 @@ pe_status batch_build(const pe_job *jobs, size_t njobs, DevBuf &arena, BatchImag
             }
         }
     }
-    std::stable_sort(items.begin(), items.end(), [&](const QItem &a, const QItem &b) {
-        if (a.cls != b.cls) {
-            const double ma = cls_max[a.cls], mb = cls_max[b.cls];
-            return ma != mb ? ma > mb : a.cls > b.cls;
-        }
-        return a.cost > b.cost;
+    {   // class order: decreasing largest item (ties by class code), looked up once per item
+        std::vector<std::pair<double, uint32_t>> order;
+        for (const auto &kv : cls_max) order.push_back({kv.second, kv.first});
+        std::sort(order.begin(), order.end(), [](const auto &a, const auto &b) {
+            return a.first != b.first ? a.first > b.first : a.second > b.second;
+        });
+        uint32_t rank_of[256] = {};
+        for (size_t r = 0; r < order.size(); ++r) rank_of[order[r].second & 255] = (uint32_t)r;
+        for (QItem &q : items) q.cls = rank_of[q.cls & 255] << 8 | (q.cls & 255);   // rank above the code
+    }
+    std::stable_sort(items.begin(), items.end(), [](const QItem &a, const QItem &b) {
+        return a.cls != b.cls ? a.cls < b.cls : a.cost > b.cost;
     });
+    for (QItem &q : items) q.cls &= 255;
     const size_t off_items = U.take(std::max<size_t>(items.size(), 1) * sizeof(uint2));
     // Counters (and the queue head) in one contiguous scratch block, cleared before each launch.
     const size_t cnt0 = S.off;
