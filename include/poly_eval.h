@@ -395,7 +395,9 @@ pe_status poly_eval_tune_load(const char *path);
  * Server: continuous batching of evaluation requests.  Requests are
  * admitted by device memory, polynomials can stay resident across
  * requests, and admitted jobs are packed into persistent-kernel epochs
- * that overlap on up to four streams (four by default).
+ * that overlap on up to four streams (four by default).  While other epochs
+ * run, an epoch of fewer than 16 ready requests waits until 16 are ready or
+ * its oldest request is 2 ms old (larger epochs use the GPU better).
  * ---------------------------------------------------------------------- */
 typedef struct {
     uint64_t mem_cap_bytes;   /* cap on resident terms + scratch + outputs */
