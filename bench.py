@@ -1035,7 +1035,7 @@ class PinnedRing:
 def run_served(args, pool=None):
     """Served workload: requests drawn from the batched mixture (30% reuse a
     resident polynomial at a new beta).  Three measurements: a burst submitted
-    back to back (throughput at saturation), the same requests through the plain
+    back to back (throughput at saturation; the median of three), the same requests through the plain
     path one by one (create, run into host memory, destroy), and a Poisson
     stream at 0.7x the burst's request rate (or --serve-rate) for latency below
     saturation.  Requests in the stored seeded sample (~1%) are compared with
@@ -1113,10 +1113,20 @@ def run_served(args, pool=None):
     srv = pe.Server(mem_cap_bytes=40 << 30, streams=args.serve_streams, max_epoch_jobs=args.serve_epoch_jobs)
     drive(burst[:50], srv, False)                      # warm-up
     srv.close()
-    srv = pe.Server(mem_cap_bytes=40 << 30, streams=args.serve_streams, max_epoch_jobs=args.serve_epoch_jobs)
-    t_burst, tp_burst, chk_burst = drive(burst, srv, False)
-    st_burst = srv.stats()
-    srv.close()
+    # three bursts, each on a fresh server; the median one is reported (a burst
+    # lasts well under a second and single bursts spread widely)
+    runs = []
+    for _ in range(3):
+        srv = pe.Server(mem_cap_bytes=40 << 30, streams=args.serve_streams, max_epoch_jobs=args.serve_epoch_jobs)
+        t_b, tp_b, chk_b = drive(burst, srv, False)
+        runs.append((t_b, tp_b, chk_b, srv.stats()))
+        srv.close()
+    runs.sort(key=lambda r: r[0])
+    t_burst, tp_burst, _, st_burst = runs[1]
+    burst_rates = [len(burst) / r[0] for r in runs]
+    # the sampled requests of all three bursts are checked
+    chk_burst = {k: sum(r[2][k] for r in runs) for k in ("checked", "matched", "without_record")}
+    chk_burst["identical"] = (chk_burst["matched"] == chk_burst["checked"]) if chk_burst["checked"] else None
     # (2) the plain path, one request at a time
     polys = {}
     t0 = time.perf_counter()
@@ -1148,7 +1158,7 @@ def run_served(args, pool=None):
         "burst": {"requests": len(burst), "seconds": t_burst, "term_points_per_s": tp_burst / t_burst,
                   "requests_per_s": capacity, "p50_ms": st_burst["p50_ms"],
                   "p99_ms": st_burst["p99_ms"], "epochs": st_burst["epochs"], "rejected": st_burst["rejected"],
-                  "oracle_check": chk_burst},
+                  "requests_per_s_of_three_bursts": burst_rates, "oracle_check": chk_burst},
         "plain_per_request": {"requests": len(burst), "seconds": t_plain, "term_points_per_s": tp_plain / t_plain,
                               "requests_per_s": len(burst) / t_plain},
         "served_over_plain": (tp_burst / t_burst) / (tp_plain / t_plain),
