@@ -964,6 +964,7 @@ def run_batched(args, print_line=True):
                            "T in {64,256,1024,2048}, 50/62-bit primes",
                "term_points": tp, "batched_term_points_per_s": v_batch, "ms_per_launch": statistics.mean(ms_batch),
                "plain_loop_term_points_per_s": v_loop, "plain_loop_ms": statistics.mean(ms_loop),
+               "ms_per_step": {"batched": [round(x, 3) for x in ms_batch], "plain_loop": [round(x, 3) for x in ms_loop]},
                "batched_over_plain_loop": v_batch / v_loop, "launches_batched": bl["kernels"],
                "plain_run_jobs": bl["plain_jobs"], "launches_plain_loop": launches_loop,
                "oracle_check_batched": check_batch, "oracle_check_plain_loop": check_loop,
