@@ -843,12 +843,6 @@ def run_ours(args):
             line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.config)
             line["cpu_baseline_definition_all_cores"] = cpu_baseline_all_cores(args.config, definition=True)
     if world == 1 and not args.no_extras:
-        # The served section runs first among the extras: right after the
-        # batched section, bursts of the served mixture ran at 1,700-3,600
-        # requests/s for several bursts against 5,300-5,800 in a fresh process
-        # (SM clocks at their maximum throughout; releasing PyTorch's cached
-        # memory did not help).
-        line["served"] = run_served(args)
         line["sparse_images"] = bench_compact(pe, out, torch)
         line["interpolation"] = bench_interp(pe, torch, mhz)
         if args.config == "large":
@@ -871,6 +865,7 @@ def run_ours(args):
         bargs = argparse.Namespace(**vars(args))
         bargs.steps, bargs.warmup = 4, 2
         line["batched"] = run_batched(bargs, print_line=False)
+        line["served"] = run_served(args)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
