@@ -65,3 +65,33 @@ def test_output_ring_never_hands_out_a_live_region():
         while ring.regions and rnd.random() < 0.3:
             wait_oldest()
     assert exact_fills > 0          # the case that must read as full did occur
+
+
+def test_served_section_child_and_fallback(monkeypatch):
+    # The default line measures the served section in a child process with this
+    # run's serving options; a failing child falls back to this process.
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--serve-seconds", "6", "--serve-burst", "1500",
+                                      "--serve-streams", "2", "--serve-epoch-jobs", "32", "--serve-rate", "900"])
+    args = bench.parse()
+    argv = bench.served_child_argv(args)
+    assert argv[1] == os.path.join(ROOT, "bench.py")
+    monkeypatch.setattr(sys, "argv", argv[1:])
+    child = bench.parse()
+    assert child.config == "served"
+    for k in ("batch_count", "serve_seconds", "serve_rate", "serve_burst", "serve_streams", "serve_epoch_jobs"):
+        assert getattr(child, k) == getattr(args, k), k
+
+    class Done:
+        def __init__(self, rc, out, err=""):
+            self.returncode, self.stdout, self.stderr = rc, out, err
+
+    line = {"metric": "served", "served_over_plain": 3.2, "burst": {"requests": 1500}}
+    monkeypatch.setattr(bench.subprocess, "run", lambda *a, **k: Done(0, "note\n" + json.dumps(line) + "\n"))
+    got = bench.served_in_child(args)
+    assert got["served_over_plain"] == 3.2 and "metric" not in got and got["process"].startswith("child")
+    monkeypatch.setattr(bench.subprocess, "run", lambda *a, **k: Done(1, "", "Traceback\nRuntimeError: boom"))
+    monkeypatch.setattr(bench, "run_served", lambda a, pool=None: {"served_over_plain": 2.0})
+    got = bench.served_in_child(args)
+    assert got["served_over_plain"] == 2.0 and got["process"].startswith("this process") and "boom" in got["process"]
